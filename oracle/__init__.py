@@ -1,0 +1,223 @@
+"""CPU oracle for augmented-neighbourhood-graph ANN search (arXiv:1312.3062).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the benchmark's CPU-baseline / reference legs may import this package.
+It wraps ``oracle.c`` (plain C, fp64 / exact integers) through ctypes and
+shares no code with the CUDA library.
+
+Functions and the passages they follow:
+  exact_knn      Sec. 2 (NN definition), Sec. 5.1 (ground truth by linear scan)
+  knn_graph      Sec. 3.1 / Sec. 5.3 (R-NN neighbourhood graph), exact
+  kmeans         Sec. 3.2 / Sec. 4.1 (PQ dictionaries per part, Lloyd, fp64)
+  round_centers  reading of Sec. 4.1 for byte data (centres rounded to bytes)
+  multiseq       Sec. 3.3 (multi-sequence algorithm)
+  bridge_graph   Sec. 4.1 (top-t bridges per ref, top-b refs per bridge)
+  search         Sec. 4.2, Algorithm 1 (ANN search over the augmented graph)
+  recall_at_k    Sec. 5.1 (accuracy r/k)
+Every function is pinned by the ``-m "not gpu"`` tests in ``tests/``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+U8, F32 = 0, 1
+STAT_NAMES = ("discovered", "ref_pops", "bridge_pops", "nonempty_bridge_pops", "max_q",
+              "max_frontier", "ms_pushes")
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (plain gcc, no FMA contraction)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-ffp-contract=off",
+                           "-o", tmp, _SRC, "-lpthread", "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64, i32 = ctypes.c_int64, ctypes.c_int
+            lib.oracle_exact_knn.argtypes = [P, i64, P, i64, i32, i32, i32, i32, P, P]
+            lib.oracle_exact_knn.restype = None
+            lib.oracle_kmeans.argtypes = [P, i64, i32, i32, i32, i32, i32, P, P]
+            lib.oracle_kmeans.restype = None
+            lib.oracle_multiseq.argtypes = [P, i32, i32, i32, i64, P, P, P, P]
+            lib.oracle_multiseq.restype = i64
+            lib.oracle_bridge_graph.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, P, P, P]
+            lib.oracle_bridge_graph.restype = i64
+            lib.oracle_search.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P, P, P,
+                                          i64, P, P, i32, P, P, P, P, i32, i32]
+            lib.oracle_search.restype = i32
+            lib.oracle_num_stats.restype = i32
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dtype_code(X: np.ndarray) -> int:
+    if X.dtype == np.uint8:
+        return U8
+    if X.dtype == np.float32:
+        return F32
+    raise TypeError(f"unsupported dtype {X.dtype}")
+
+
+def exact_knn(X: np.ndarray, Qs: np.ndarray, k: int, exclude_self: bool = False):
+    """Linear-scan k-NN by (squared distance, id); pads with -1 / +inf."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    Qs = np.ascontiguousarray(Qs)
+    assert X.dtype == Qs.dtype and X.shape[1] == Qs.shape[1]
+    nq = Qs.shape[0]
+    ids = np.empty((nq, k), np.int32)
+    keys = np.empty((nq, k), np.float64)
+    lib.oracle_exact_knn(_ptr(X), X.shape[0], _ptr(Qs), nq, X.shape[1], _dtype_code(X), k,
+                         int(exclude_self), _ptr(ids), _ptr(keys))
+    return ids, keys
+
+
+def knn_graph(X: np.ndarray, R: int):
+    """Exact R-NN graph: each row ascending by (key, id), self excluded."""
+    return exact_knn(X, X, R, exclude_self=True)
+
+
+def kmeans(X: np.ndarray, P: int, n: int, iters: int, init_rows: np.ndarray) -> np.ndarray:
+    """Per-part Lloyd k-means in fp64; returns centres of shape (P, n, d/P) float64."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    N, d = X.shape
+    assert d % P == 0
+    init_rows = np.ascontiguousarray(init_rows, dtype=np.int64)
+    assert init_rows.shape == (n,) and len(np.unique(init_rows)) == n
+    C = np.empty((P, n, d // P), np.float64)
+    lib.oracle_kmeans(_ptr(X), N, d, _dtype_code(X), P, n, iters, _ptr(init_rows), _ptr(C))
+    return C
+
+
+def round_centers(C: np.ndarray, dtype) -> np.ndarray:
+    """Store the fp64 centres in the data type: bytes by round-half-even and clip."""
+    if np.dtype(dtype) == np.uint8:
+        return np.clip(np.rint(C), 0, 255).astype(np.uint8)
+    return C.astype(np.float32)
+
+
+def multiseq(part_keys: np.ndarray, dtype, m: int):
+    """First m bridges in multi-sequence order for part keys of shape (P, n).
+
+    Returns (keys, bridge_ids, ranks (m, P), stats {max_frontier, pushes})."""
+    lib = _load()
+    part_keys = np.ascontiguousarray(part_keys, dtype=np.float64)
+    P, n = part_keys.shape
+    keys = np.empty(m, np.float64)
+    ids = np.empty(m, np.uint64)
+    ranks = np.empty((m, P), np.int32)
+    st = np.zeros(2, np.int64)
+    got = lib.oracle_multiseq(_ptr(part_keys), P, n, U8 if np.dtype(dtype) == np.uint8 else F32,
+                              m, _ptr(keys), _ptr(ids), _ptr(ranks), _ptr(st))
+    return keys[:got], ids[:got], ranks[:got], {"max_frontier": int(st[0]), "pushes": int(st[1])}
+
+
+def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int):
+    """Bridge graph: dict with ascending 'bridges' (uint64), CSR 'offsets', 'refs', 'keys'."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    centers = np.ascontiguousarray(centers)
+    assert centers.dtype == X.dtype
+    P, n, dp = centers.shape
+    N, d = X.shape
+    assert dp * P == d
+    cap = N * t
+    bridges = np.empty(cap, np.uint64)
+    offsets = np.empty(cap + 1, np.int64)
+    refs = np.empty(cap, np.int32)
+    keys = np.empty(cap, np.float64)
+    M = lib.oracle_bridge_graph(_ptr(X), N, d, _dtype_code(X), P, n, _ptr(centers), t, b,
+                                _ptr(bridges), _ptr(offsets), _ptr(refs), _ptr(keys))
+    nnz = int(offsets[M])
+    return {"bridges": bridges[:M].copy(), "offsets": offsets[:M + 1].copy(),
+            "refs": refs[:nnz].copy(), "keys": keys[:nnz].copy(), "P": P, "n": n}
+
+
+def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, queries: np.ndarray,
+           k, T, kmax: int | None = None, nthreads: int = 1, trace: bool = False):
+    """Algorithm 1 for each query.  k, T: scalars or per-query arrays.
+
+    Returns (ids (nq, kmax) int32, keys (nq, kmax) float64, stats dict of arrays);
+    with trace=True the stats dict also holds 'trace' (nq, max T): the
+    discovered ids in discovery order, -1 after the last."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    queries = np.ascontiguousarray(queries)
+    graph = np.ascontiguousarray(graph, dtype=np.int32)
+    centers = np.ascontiguousarray(centers)
+    assert X.dtype == queries.dtype == centers.dtype
+    N, d = X.shape
+    nq = queries.shape[0]
+    P, n, _ = centers.shape
+    k = np.ascontiguousarray(np.broadcast_to(np.asarray(k, np.int32), (nq,)))
+    T = np.ascontiguousarray(np.broadcast_to(np.asarray(T, np.int32), (nq,)))
+    if kmax is None:
+        kmax = int(k.max()) if nq else 1
+    ids = np.empty((nq, kmax), np.int32)
+    keys = np.empty((nq, kmax), np.float64)
+    ns = lib.oracle_num_stats()
+    st = np.zeros((nq, ns), np.int64)
+    bridges = np.ascontiguousarray(bg["bridges"], dtype=np.uint64)
+    offs = np.ascontiguousarray(bg["offsets"], dtype=np.int64)
+    refs = np.ascontiguousarray(bg["refs"], dtype=np.int32)
+    cap = int(T.max()) if (trace and nq) else 0
+    disc = np.empty((nq, max(cap, 1)), np.int32)
+    rc = lib.oracle_search(_ptr(X), N, d, _dtype_code(X), _ptr(graph), graph.shape[1], P, n,
+                           _ptr(centers), len(bridges), _ptr(bridges), _ptr(offs), _ptr(refs),
+                           _ptr(queries), nq, _ptr(k), _ptr(T), kmax, _ptr(ids), _ptr(keys),
+                           _ptr(st), _ptr(disc) if trace else None, cap, nthreads)
+    if rc != 0:
+        raise ValueError("oracle_search: bad arguments")
+    out = {name: st[:, i] for i, name in enumerate(STAT_NAMES)}
+    if trace:
+        out["trace"] = disc[:, :cap]
+    return ids, keys, out
+
+
+def recall_at_k(found_ids: np.ndarray, true_keys: np.ndarray, X: np.ndarray, queries: np.ndarray,
+                k: int) -> np.ndarray:
+    """Accuracy r/k per query (Sec. 5.1), tie-tolerant: a returned id counts when
+    its true key is <= the true k-th key.  found_ids: (nq, >=k)."""
+    nq = found_ids.shape[0]
+    out = np.zeros(nq)
+    for i in range(nq):
+        ids = found_ids[i, :k]
+        ids = ids[ids >= 0]
+        if len(ids) == 0:
+            continue
+        kth = true_keys[i, k - 1]
+        if X.dtype == np.uint8:
+            diff = X[ids].astype(np.int64) - queries[i].astype(np.int64)
+            dk = (diff * diff).sum(1).astype(np.float64)
+        else:
+            diff = X[ids].astype(np.float64) - queries[i].astype(np.float64)
+            dk = (diff * diff).sum(1).astype(np.float32).astype(np.float64)
+        out[i] = np.count_nonzero(dk <= kth) / k
+    return out

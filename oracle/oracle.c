@@ -1,0 +1,752 @@
+/*
+ * oracle.c -- CPU oracle for "Fast Neighborhood Graph Search using Cartesian
+ * Concatenation" (Wang, Wang, Zeng, Tu, Gan, Li; arXiv:1312.3062).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously-correct
+ * statement of what the GPU path computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may build, load or call it.  It
+ * shares no code, header or table with the CUDA library.
+ *
+ * Conventions (the paper is silent on these; each reading is fixed here):
+ *  - Every key is a SQUARED Euclidean distance (Sec. 2 defines dist as L2;
+ *    Sec. 3.2 stores squared distances in the part tables; Sec. 4.2 sums
+ *    squared part distances).  Squared keys order candidates exactly like
+ *    dist() does, so Alg. 1's results are unchanged.
+ *  - uint8 data: keys are exact integers.
+ *  - float32 data: a key is computed in fp64 and then rounded to the nearest
+ *    float32; every comparison is taken on that float32 value (the kernel's
+ *    precision), so both implementations order candidates identically.
+ *    A bridge key is the float32 sum of the part keys added left to right.
+ *  - Main queue order: (key, kind, id), kind ref = 0 < bridge = 1.
+ *  - Result set: the k smallest by (key, id), returned ascending, padded with
+ *    id -1 / key +inf when fewer than k points were discovered.
+ *  - Budget: t counts discovered reference vectors; discovery stops the
+ *    moment t reaches T, even inside an adjacency list, and the search ends.
+ *  - Part p covers the contiguous dims [p*dp, (p+1)*dp), dp = d / P.
+ *  - Part sort order: (part key, center id).  Bridge order in the
+ *    multi-sequence: (bridge key, rank tuple compared lexicographically with
+ *    part 0 first).  Bridge id: mixed radix of the ORIGINAL center ids with
+ *    part 0 most significant.
+ *  - Multi-sequence push rule: a tuple is pushed once all of its immediate
+ *    predecessors (one rank lowered by one) have been POPPED.
+ *  - kNN rows: ascending (key, id), self excluded.  Bridge lists: ascending
+ *    (key to the bridge, ref id).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { DT_U8 = 0, DT_F32 = 1 };
+
+/* ------------------------------------------------------------------------ */
+/* Distances (Sec. 2: dist(q, x) = ||q - x||_2; Sec. 3.2: squared tables)    */
+/* ------------------------------------------------------------------------ */
+
+/* Squared L2 between a[0..len) and b[0..len) of the given dtype. */
+static double sqdist(const void *a, const void *b, int len, int dtype) {
+    if (dtype == DT_U8) {
+        const uint8_t *x = (const uint8_t *)a, *y = (const uint8_t *)b;
+        int64_t s = 0;
+        for (int i = 0; i < len; i++) {
+            int64_t t = (int64_t)x[i] - (int64_t)y[i];
+            s += t * t;
+        }
+        return (double)s;
+    } else {
+        const float *x = (const float *)a, *y = (const float *)b;
+        double s = 0.0;
+        for (int i = 0; i < len; i++) {
+            double t = (double)x[i] - (double)y[i];
+            s += t * t;
+        }
+        return (double)(float)s; /* decisions are taken at float32 */
+    }
+}
+
+static const void *row_ptr(const void *base, int64_t row, int len, int dtype) {
+    if (dtype == DT_U8) return (const uint8_t *)base + row * (int64_t)len;
+    return (const float *)base + row * (int64_t)len;
+}
+
+/* Bridge key from P part keys (Sec. 4.2: dist^2(q, y) = sum_p dist^2(q^p, y^p)). */
+static double bridge_key(const double *part_keys, int P, int dtype) {
+    if (dtype == DT_U8) {
+        double s = 0.0; /* integers far below 2^53: exact */
+        for (int p = 0; p < P; p++) s += part_keys[p];
+        return s;
+    } else {
+        float s = (float)part_keys[0];
+        for (int p = 1; p < P; p++) s = s + (float)part_keys[p];
+        return (double)s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Top-k selection by (key, id)                                              */
+/* ------------------------------------------------------------------------ */
+
+static int pair_less(double ka, int64_t ia, double kb, int64_t ib) {
+    return ka < kb || (ka == kb && ia < ib);
+}
+
+/* Insert (key, id) into the ascending list (keys, ids) of length *len, kept to
+   at most cap entries. */
+static void topk_insert(double *keys, int64_t *ids, int *len, int cap, double key, int64_t id) {
+    int n = *len;
+    if (n == cap) {
+        if (!pair_less(key, id, keys[n - 1], ids[n - 1])) return;
+        n--; /* drop the current largest */
+    }
+    int pos = n;
+    while (pos > 0 && pair_less(key, id, keys[pos - 1], ids[pos - 1])) {
+        keys[pos] = keys[pos - 1];
+        ids[pos] = ids[pos - 1];
+        pos--;
+    }
+    keys[pos] = key;
+    ids[pos] = id;
+    *len = n + 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exact k nearest neighbours by linear scan (Sec. 2; Sec. 5.1 ground truth) */
+/* and the exact R-NN neighbourhood graph (Sec. 3.1, Sec. 5.3).              */
+/* ------------------------------------------------------------------------ */
+
+/* For each query row i of Qs, the k nearest rows of X by (key, id).  When
+   exclude_self is set, Qs must be X and row i is skipped for query i.
+   Rows with fewer than k candidates are padded with id -1 / key +inf. */
+void oracle_exact_knn(const void *X, int64_t N, const void *Qs, int64_t nq, int d, int dtype,
+                      int k, int exclude_self, int32_t *out_ids, double *out_keys) {
+    double *keys = (double *)malloc(sizeof(double) * (size_t)k);
+    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
+    for (int64_t i = 0; i < nq; i++) {
+        int len = 0;
+        const void *q = row_ptr(Qs, i, d, dtype);
+        for (int64_t j = 0; j < N; j++) {
+            if (exclude_self && j == i) continue;
+            double key = sqdist(q, row_ptr(X, j, d, dtype), d, dtype);
+            topk_insert(keys, ids, &len, k, key, j);
+        }
+        for (int r = 0; r < k; r++) {
+            out_ids[i * k + r] = r < len ? (int32_t)ids[r] : -1;
+            out_keys[i * k + r] = r < len ? keys[r] : INFINITY;
+        }
+    }
+    free(keys);
+    free(ids);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Subvector dictionaries: product-quantization k-means per part             */
+/* (Sec. 3.2; Sec. 4.1 "Computing bridge vectors")                          */
+/* ------------------------------------------------------------------------ */
+
+/* Lloyd's algorithm in fp64 on each contiguous part independently.
+   init_rows: n distinct training-row indices; center j of every part starts
+   at row init_rows[j].  Assignment ties go to the lower center id; an empty
+   cluster keeps its previous center.  centers: out, P*n*dp doubles. */
+void oracle_kmeans(const void *X, int64_t N, int d, int dtype, int P, int n, int iters,
+                   const int64_t *init_rows, double *centers) {
+    int dp = d / P;
+    double *sums = (double *)malloc(sizeof(double) * (size_t)n * dp);
+    int64_t *counts = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int32_t *assign = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    double *row = (double *)malloc(sizeof(double) * (size_t)dp);
+    for (int p = 0; p < P; p++) {
+        double *C = centers + (int64_t)p * n * dp;
+        for (int j = 0; j < n; j++)
+            for (int e = 0; e < dp; e++) {
+                int64_t at = init_rows[j] * d + p * dp + e;
+                C[j * dp + e] = dtype == DT_U8 ? (double)((const uint8_t *)X)[at]
+                                               : (double)((const float *)X)[at];
+            }
+        for (int it = 0; it < iters; it++) {
+            /* assignment step */
+            for (int64_t i = 0; i < N; i++) {
+                for (int e = 0; e < dp; e++) {
+                    int64_t at = i * d + p * dp + e;
+                    row[e] = dtype == DT_U8 ? (double)((const uint8_t *)X)[at]
+                                            : (double)((const float *)X)[at];
+                }
+                double best = INFINITY;
+                int arg = 0;
+                for (int j = 0; j < n; j++) {
+                    double s = 0.0;
+                    for (int e = 0; e < dp; e++) {
+                        double t = row[e] - C[j * dp + e];
+                        s += t * t;
+                    }
+                    if (s < best) { best = s; arg = j; }
+                }
+                assign[i] = arg;
+            }
+            /* update step */
+            memset(sums, 0, sizeof(double) * (size_t)n * dp);
+            memset(counts, 0, sizeof(int64_t) * (size_t)n);
+            for (int64_t i = 0; i < N; i++) {
+                int j = assign[i];
+                counts[j]++;
+                for (int e = 0; e < dp; e++) {
+                    int64_t at = i * d + p * dp + e;
+                    sums[j * dp + e] += dtype == DT_U8 ? (double)((const uint8_t *)X)[at]
+                                                       : (double)((const float *)X)[at];
+                }
+            }
+            for (int j = 0; j < n; j++)
+                if (counts[j] > 0)
+                    for (int e = 0; e < dp; e++) C[j * dp + e] = sums[j * dp + e] / (double)counts[j];
+        }
+    }
+    free(sums);
+    free(counts);
+    free(assign);
+    free(row);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-part tables and their sort (Sec. 4.2, first step of the query)        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int P, n, dtype;
+    double *key;    /* P*n part keys, unsorted: key[p*n + c] */
+    double *skey;   /* P*n sorted part keys: skey[p*n + rank] */
+    int32_t *scid;  /* P*n center id at each rank */
+} tables_t;
+
+typedef struct { double key; int32_t cid; } kc_t;
+
+static int kc_cmp(const void *a, const void *b) {
+    const kc_t *x = (const kc_t *)a, *y = (const kc_t *)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return (x->cid > y->cid) - (x->cid < y->cid);
+}
+
+/* Distances from the parts of vec to every center, then each part sorted by
+   (key, center id). */
+static void tables_build(tables_t *tb, const void *vec, int d, int dtype, int P, int n,
+                         const void *centers) {
+    int dp = d / P;
+    tb->P = P;
+    tb->n = n;
+    tb->dtype = dtype;
+    kc_t *tmp = (kc_t *)malloc(sizeof(kc_t) * (size_t)n);
+    for (int p = 0; p < P; p++) {
+        const void *qpart = dtype == DT_U8 ? (const void *)((const uint8_t *)vec + p * dp)
+                                           : (const void *)((const float *)vec + p * dp);
+        for (int c = 0; c < n; c++) {
+            const void *cent = row_ptr(centers, (int64_t)p * n + c, dp, dtype);
+            double k = sqdist(qpart, cent, dp, dtype);
+            tb->key[p * n + c] = k;
+            tmp[c].key = k;
+            tmp[c].cid = c;
+        }
+        qsort(tmp, (size_t)n, sizeof(kc_t), kc_cmp);
+        for (int r = 0; r < n; r++) {
+            tb->skey[p * n + r] = tmp[r].key;
+            tb->scid[p * n + r] = tmp[r].cid;
+        }
+    }
+    free(tmp);
+}
+
+static tables_t tables_alloc(int P, int n) {
+    tables_t tb;
+    tb.key = (double *)malloc(sizeof(double) * (size_t)P * n);
+    tb.skey = (double *)malloc(sizeof(double) * (size_t)P * n);
+    tb.scid = (int32_t *)malloc(sizeof(int32_t) * (size_t)P * n);
+    tb.P = P;
+    tb.n = n;
+    tb.dtype = 0;
+    return tb;
+}
+
+static void tables_free(tables_t *tb) {
+    free(tb->key);
+    free(tb->skey);
+    free(tb->scid);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-sequence enumeration (Sec. 3.3; ExtractNextNearestBridgeVector)     */
+/* ------------------------------------------------------------------------ */
+
+#define MAXP 8
+
+typedef struct { double key; int32_t r[MAXP]; } ms_item;
+
+typedef struct {
+    const tables_t *tb;
+    ms_item *heap;
+    int64_t hlen, hcap;
+    uint64_t *set; /* open-addressing set of popped rank codes (code + 1; 0 = empty) */
+    int64_t scap, slen;
+    int64_t max_frontier;
+    int64_t npushed;
+} mseq_t;
+
+static int ms_less(const ms_item *a, const ms_item *b, int P) {
+    if (a->key < b->key) return 1;
+    if (a->key > b->key) return 0;
+    for (int p = 0; p < P; p++) {
+        if (a->r[p] < b->r[p]) return 1;
+        if (a->r[p] > b->r[p]) return 0;
+    }
+    return 0;
+}
+
+static uint64_t ms_code(const int32_t *r, int P, int n) {
+    uint64_t c = 0;
+    for (int p = 0; p < P; p++) c = c * (uint64_t)n + (uint64_t)r[p];
+    return c;
+}
+
+static uint64_t mix64(uint64_t x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33;
+    return x;
+}
+
+static int set_has(const mseq_t *m, uint64_t code) {
+    uint64_t mask = (uint64_t)m->scap - 1, h = mix64(code) & mask;
+    while (m->set[h]) {
+        if (m->set[h] == code + 1) return 1;
+        h = (h + 1) & mask;
+    }
+    return 0;
+}
+
+static void set_add(mseq_t *m, uint64_t code) {
+    if (2 * (m->slen + 1) > m->scap) {
+        uint64_t *old = m->set;
+        int64_t oc = m->scap;
+        m->scap *= 2;
+        m->set = (uint64_t *)calloc((size_t)m->scap, sizeof(uint64_t));
+        m->slen = 0;
+        for (int64_t i = 0; i < oc; i++)
+            if (old[i]) set_add(m, old[i] - 1);
+        free(old);
+    }
+    uint64_t mask = (uint64_t)m->scap - 1, h = mix64(code) & mask;
+    while (m->set[h]) {
+        if (m->set[h] == code + 1) return;
+        h = (h + 1) & mask;
+    }
+    m->set[h] = code + 1;
+    m->slen++;
+}
+
+static void ms_push(mseq_t *m, const int32_t *r) {
+    const tables_t *tb = m->tb;
+    int P = tb->P;
+    ms_item it;
+    double parts[MAXP] = {0};
+    for (int p = 0; p < P; p++) {
+        it.r[p] = r[p];
+        parts[p] = tb->skey[p * tb->n + r[p]];
+    }
+    it.key = bridge_key(parts, P, tb->dtype);
+    if (m->hlen == m->hcap) {
+        m->hcap *= 2;
+        m->heap = (ms_item *)realloc(m->heap, sizeof(ms_item) * (size_t)m->hcap);
+    }
+    int64_t i = m->hlen++;
+    m->heap[i] = it;
+    while (i > 0) {
+        int64_t par = (i - 1) / 2;
+        if (!ms_less(&m->heap[i], &m->heap[par], P)) break;
+        ms_item t = m->heap[i]; m->heap[i] = m->heap[par]; m->heap[par] = t;
+        i = par;
+    }
+    m->npushed++;
+    if (m->hlen > m->max_frontier) m->max_frontier = m->hlen;
+}
+
+static void ms_init(mseq_t *m, const tables_t *tb) {
+    m->tb = tb;
+    m->hcap = 64;
+    m->hlen = 0;
+    m->heap = (ms_item *)malloc(sizeof(ms_item) * (size_t)m->hcap);
+    m->scap = 64;
+    m->slen = 0;
+    m->set = (uint64_t *)calloc((size_t)m->scap, sizeof(uint64_t));
+    m->max_frontier = 0;
+    m->npushed = 0;
+    int32_t zero[MAXP] = {0};
+    ms_push(m, zero); /* start from the tuple of first ranks */
+}
+
+static void ms_free(mseq_t *m) {
+    free(m->heap);
+    free(m->set);
+}
+
+/* Pop the next tuple in (key, ranks) order.  Returns 0 when every tuple has
+   been produced. */
+static int ms_next(mseq_t *m, ms_item *out) {
+    const tables_t *tb = m->tb;
+    int P = tb->P, n = tb->n;
+    if (m->hlen == 0) return 0;
+    *out = m->heap[0];
+    m->heap[0] = m->heap[--m->hlen];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, s = i;
+        if (l < m->hlen && ms_less(&m->heap[l], &m->heap[s], P)) s = l;
+        if (r < m->hlen && ms_less(&m->heap[r], &m->heap[s], P)) s = r;
+        if (s == i) break;
+        ms_item t = m->heap[i]; m->heap[i] = m->heap[s]; m->heap[s] = t;
+        i = s;
+    }
+    set_add(m, ms_code(out->r, P, n));
+    /* Successors: raise one rank by one; push once every predecessor of the
+       successor (each of its nonzero ranks lowered by one) has been popped. */
+    for (int b = 0; b < P; b++) {
+        if (out->r[b] + 1 >= n) continue;
+        int32_t v[MAXP];
+        for (int p = 0; p < P; p++) v[p] = out->r[p];
+        v[b]++;
+        int ready = 1;
+        for (int c = 0; c < P && ready; c++) {
+            if (c == b || v[c] == 0) continue;
+            v[c]--;
+            if (!set_has(m, ms_code(v, P, n))) ready = 0;
+            v[c]++;
+        }
+        if (ready) ms_push(m, v);
+    }
+    return 1;
+}
+
+static uint64_t bridge_id_of(const tables_t *tb, const int32_t *ranks) {
+    uint64_t id = 0;
+    for (int p = 0; p < tb->P; p++) id = id * (uint64_t)tb->n + (uint64_t)tb->scid[p * tb->n + ranks[p]];
+    return id;
+}
+
+/* First m bridges of the multi-sequence for the unsorted part keys
+   `part_keys` (P*n).  Writes bridge keys, bridge ids (center-id mixed radix)
+   and rank tuples (m*P).  Returns how many were produced (< m only when all
+   n^P were exhausted).  stats (optional, 2 values): max frontier, pushes. */
+int64_t oracle_multiseq(const double *part_keys, int P, int n, int dtype, int64_t m,
+                        double *out_keys, uint64_t *out_ids, int32_t *out_ranks, int64_t *stats) {
+    tables_t tb = tables_alloc(P, n);
+    tb.dtype = dtype;
+    kc_t *tmp = (kc_t *)malloc(sizeof(kc_t) * (size_t)n);
+    for (int p = 0; p < P; p++) {
+        for (int c = 0; c < n; c++) {
+            tb.key[p * n + c] = part_keys[p * n + c];
+            tmp[c].key = part_keys[p * n + c];
+            tmp[c].cid = c;
+        }
+        qsort(tmp, (size_t)n, sizeof(kc_t), kc_cmp);
+        for (int r = 0; r < n; r++) {
+            tb.skey[p * n + r] = tmp[r].key;
+            tb.scid[p * n + r] = tmp[r].cid;
+        }
+    }
+    free(tmp);
+    mseq_t ms;
+    ms_init(&ms, &tb);
+    int64_t got = 0;
+    ms_item it;
+    while (got < m && ms_next(&ms, &it)) {
+        out_keys[got] = it.key;
+        out_ids[got] = bridge_id_of(&tb, it.r);
+        for (int p = 0; p < P; p++) out_ranks[got * P + p] = it.r[p];
+        got++;
+    }
+    if (stats) {
+        stats[0] = ms.max_frontier;
+        stats[1] = ms.npushed;
+    }
+    ms_free(&ms);
+    tables_free(&tb);
+    return got;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bridge graph (Sec. 4.1 "Augmented neighborhood graph")                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t bridge; double key; int32_t ref; } triple_t;
+
+static int triple_cmp(const void *a, const void *b) {
+    const triple_t *x = (const triple_t *)a, *y = (const triple_t *)b;
+    if (x->bridge != y->bridge) return x->bridge < y->bridge ? -1 : 1;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->ref > y->ref) - (x->ref < y->ref);
+}
+
+/* For each reference vector, its top-t bridges (in multi-sequence order);
+   then for each bridge, the b nearest of the references that named it,
+   ordered by (key, ref id).  Outputs (capacity N*t each):
+     bridges[M]     ascending bridge ids that got at least one reference,
+     offsets[M+1]   CSR offsets into refs/keys,
+     refs, keys     the kept references and their keys to the bridge.
+   Returns M. */
+int64_t oracle_bridge_graph(const void *X, int64_t N, int d, int dtype, int P, int n,
+                            const void *centers, int t, int b, uint64_t *bridges,
+                            int64_t *offsets, int32_t *refs, double *keys) {
+    triple_t *all = (triple_t *)malloc(sizeof(triple_t) * (size_t)N * (size_t)t);
+    int64_t cnt = 0;
+    tables_t tb = tables_alloc(P, n);
+    for (int64_t i = 0; i < N; i++) {
+        tables_build(&tb, row_ptr(X, i, d, dtype), d, dtype, P, n, centers);
+        mseq_t ms;
+        ms_init(&ms, &tb);
+        ms_item it;
+        for (int j = 0; j < t && ms_next(&ms, &it); j++) {
+            all[cnt].bridge = bridge_id_of(&tb, it.r);
+            all[cnt].key = it.key;
+            all[cnt].ref = (int32_t)i;
+            cnt++;
+        }
+        ms_free(&ms);
+    }
+    tables_free(&tb);
+    qsort(all, (size_t)cnt, sizeof(triple_t), triple_cmp);
+    int64_t M = 0, out = 0;
+    for (int64_t s = 0; s < cnt;) {
+        int64_t e = s;
+        while (e < cnt && all[e].bridge == all[s].bridge) e++;
+        bridges[M] = all[s].bridge;
+        offsets[M] = out;
+        for (int64_t j = s; j < e && j < s + b; j++) {
+            refs[out] = all[j].ref;
+            keys[out] = all[j].key;
+            out++;
+        }
+        M++;
+        s = e;
+    }
+    offsets[M] = out;
+    free(all);
+    return M;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1: ANN search over the augmented neighborhood graph (Sec. 4.2)  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double key; int kind; int64_t id; } q_item; /* kind 0 = ref, 1 = bridge */
+
+static int q_less(const q_item *a, const q_item *b) {
+    if (a->key != b->key) return a->key < b->key;
+    if (a->kind != b->kind) return a->kind < b->kind;
+    return a->id < b->id;
+}
+
+typedef struct { q_item *h; int64_t len, cap; } pq_t;
+
+static void pq_push(pq_t *q, q_item it) {
+    if (q->len == q->cap) {
+        q->cap = q->cap ? q->cap * 2 : 64;
+        q->h = (q_item *)realloc(q->h, sizeof(q_item) * (size_t)q->cap);
+    }
+    int64_t i = q->len++;
+    q->h[i] = it;
+    while (i > 0) {
+        int64_t p = (i - 1) / 2;
+        if (!q_less(&q->h[i], &q->h[p])) break;
+        q_item t = q->h[i]; q->h[i] = q->h[p]; q->h[p] = t;
+        i = p;
+    }
+}
+
+static q_item pq_pop(pq_t *q) {
+    q_item top = q->h[0];
+    q->h[0] = q->h[--q->len];
+    int64_t i = 0;
+    for (;;) {
+        int64_t l = 2 * i + 1, r = l + 1, s = i;
+        if (l < q->len && q_less(&q->h[l], &q->h[s])) s = l;
+        if (r < q->len && q_less(&q->h[r], &q->h[s])) s = r;
+        if (s == i) break;
+        q_item t = q->h[i]; q->h[i] = q->h[s]; q->h[s] = t;
+        i = s;
+    }
+    return top;
+}
+
+enum {
+    ST_DISCOVERED = 0, /* t at the end: reference vectors discovered */
+    ST_REF_POPS,       /* reference vectors popped (neighbourhoods expanded) */
+    ST_BRIDGE_POPS,    /* bridge vectors popped */
+    ST_NONEMPTY_POPS,  /* popped bridges with at least one reference */
+    ST_MAX_Q,          /* largest main-queue length (refs + the bridge) */
+    ST_MAX_FRONTIER,   /* largest multi-sequence queue length */
+    ST_MS_PUSHES,      /* tuples pushed into the multi-sequence queue */
+    ST_N
+};
+
+typedef struct {
+    const void *X;
+    int64_t N;
+    int d, dtype;
+    const int32_t *graph;
+    int R;
+    int P, n;
+    const void *centers;
+    int64_t M;
+    const uint64_t *bridges;
+    const int64_t *boff;
+    const int32_t *brefs;
+} index_t;
+
+/* Bridge id -> its reference list (binary search over the sorted ids). */
+static int64_t bridge_lookup(const index_t *ix, uint64_t id, int64_t *len) {
+    int64_t lo = 0, hi = ix->M;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (ix->bridges[mid] < id) lo = mid + 1; else hi = mid;
+    }
+    if (lo < ix->M && ix->bridges[lo] == id) {
+        *len = ix->boff[lo + 1] - ix->boff[lo];
+        return ix->boff[lo];
+    }
+    *len = 0;
+    return 0;
+}
+
+/* One query.  ids/keys: kmax outputs; stats: ST_N values. */
+static void search_one(const index_t *ix, const void *q, int k, int T, int kmax, uint8_t *color,
+                       int32_t *out_ids, double *out_keys, int64_t *stats, int32_t *disc,
+                       int disc_cap) {
+    int64_t st[ST_N] = {0};
+    /* Mark each reference vector undiscovered. */
+    memset(color, 0, (size_t)ix->N);
+    /* Tables and per-part sort, then the nearest bridge vector. */
+    tables_t tb = tables_alloc(ix->P, ix->n);
+    tables_build(&tb, q, ix->d, ix->dtype, ix->P, ix->n, ix->centers);
+    mseq_t ms;
+    ms_init(&ms, &tb);
+    pq_t Q = {0};
+    double *rkeys = (double *)malloc(sizeof(double) * (size_t)(k > 0 ? k : 1));
+    int64_t *rids = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    int rlen = 0;
+    ms_item cur;
+    int32_t cur_ranks[MAXP];
+    if (ms_next(&ms, &cur)) {
+        q_item it = {cur.key, 1, 0};
+        memcpy(cur_ranks, cur.r, sizeof(cur_ranks));
+        pq_push(&Q, it);
+    }
+    int64_t t = 0;
+    if (Q.len > st[ST_MAX_Q]) st[ST_MAX_Q] = Q.len;
+    while (Q.len > 0 && t < T) {
+        q_item p = pq_pop(&Q);
+        const int32_t *adj;
+        int64_t alen;
+        if (p.kind == 0) {
+            st[ST_REF_POPS]++;
+            adj = ix->graph + p.id * ix->R;
+            alen = ix->R;
+        } else {
+            st[ST_BRIDGE_POPS]++;
+            int64_t off = bridge_lookup(ix, bridge_id_of(&tb, cur_ranks), &alen);
+            adj = ix->brefs + off;
+            if (alen > 0) st[ST_NONEMPTY_POPS]++;
+        }
+        for (int64_t a = 0; a < alen && t < T; a++) {
+            int32_t x = adj[a];
+            if (x < 0) continue; /* padding in short kNN rows */
+            if (color[x] == 0) {
+                double D = sqdist(q, row_ptr(ix->X, x, ix->d, ix->dtype), ix->d, ix->dtype);
+                q_item it = {D, 0, x};
+                pq_push(&Q, it);
+                color[x] = 1;
+                if (k > 0) topk_insert(rkeys, rids, &rlen, k, D, x);
+                if (disc && t < disc_cap) disc[t] = x;
+                t++;
+            }
+        }
+        if (p.kind == 1 && t < T) {
+            if (ms_next(&ms, &cur)) {
+                q_item it = {cur.key, 1, 0};
+                memcpy(cur_ranks, cur.r, sizeof(cur_ranks));
+                pq_push(&Q, it);
+            }
+        }
+        if (Q.len > st[ST_MAX_Q]) st[ST_MAX_Q] = Q.len;
+    }
+    st[ST_DISCOVERED] = t;
+    st[ST_MAX_FRONTIER] = ms.max_frontier;
+    st[ST_MS_PUSHES] = ms.npushed;
+    for (int r = 0; r < kmax; r++) {
+        out_ids[r] = r < rlen ? (int32_t)rids[r] : -1;
+        out_keys[r] = r < rlen ? rkeys[r] : INFINITY;
+    }
+    if (stats) memcpy(stats, st, sizeof(st));
+    if (disc)
+        for (int64_t i = t; i < disc_cap; i++) disc[i] = -1;
+    free(rkeys);
+    free(rids);
+    free(Q.h);
+    ms_free(&ms);
+    tables_free(&tb);
+}
+
+typedef struct {
+    const index_t *ix;
+    const void *queries;
+    int64_t nq;
+    const int32_t *k, *T;
+    int kmax;
+    int32_t *out_ids;
+    double *out_keys;
+    int64_t *stats;
+    int32_t *disc;
+    int disc_cap;
+    int64_t next;
+    pthread_mutex_t mu;
+} job_t;
+
+static void *worker(void *arg) {
+    job_t *j = (job_t *)arg;
+    const index_t *ix = j->ix;
+    uint8_t *color = (uint8_t *)malloc((size_t)ix->N);
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t i = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (i >= j->nq) break;
+        search_one(ix, row_ptr(j->queries, i, ix->d, ix->dtype), j->k[i], j->T[i], j->kmax, color,
+                   j->out_ids + i * j->kmax, j->out_keys + i * j->kmax,
+                   j->stats ? j->stats + i * ST_N : NULL,
+                   j->disc ? j->disc + i * (int64_t)j->disc_cap : NULL, j->disc_cap);
+    }
+    free(color);
+    return NULL;
+}
+
+/* Batched search: one query at a time per thread (nthreads >= 1).
+   k[i], T[i]: per-query result count (<= kmax) and budget.
+   bridges/boff/brefs: the bridge graph as produced by oracle_bridge_graph.
+   disc (optional, nq*disc_cap): discovered ids in discovery order, -1 after. */
+int oracle_search(const void *X, int64_t N, int d, int dtype, const int32_t *graph, int R, int P,
+                  int n, const void *centers, int64_t M, const uint64_t *bridges,
+                  const int64_t *boff, const int32_t *brefs, const void *queries, int64_t nq,
+                  const int32_t *k, const int32_t *T, int kmax, int32_t *out_ids,
+                  double *out_keys, int64_t *stats, int32_t *disc, int disc_cap, int nthreads) {
+    if (P > MAXP || P < 1 || d % P != 0) return -1;
+    index_t ix = {X, N, d, dtype, graph, R, P, n, centers, M, bridges, boff, brefs};
+    job_t job = {&ix, queries, nq, k, T, kmax, out_ids, out_keys, stats, disc, disc_cap, 0,
+                 PTHREAD_MUTEX_INITIALIZER};
+    if (nthreads <= 1) {
+        worker(&job);
+        return 0;
+    }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, worker, &job);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+int oracle_num_stats(void) { return ST_N; }
