@@ -1,0 +1,534 @@
+#!/usr/bin/env python
+"""Benchmark: queries/s at recall@10 = 0.9 of augmented-neighbourhood-graph
+search (Algorithm 1 of arXiv:1312.3062) on one GB300, persistent vs plain vs
+served forms, with p50/p99 latency of the served form.
+
+Workload: SIFT-shaped, N = 1,000,000 x 128 uint8 references (seeded
+1,000-component Gaussian mixture), 10,000 queries from the same mixture; exact
+kNN graph R = 20 (GPU), P = 4 x n = 256 part dictionaries (GPU k-means, 10
+iterations on all rows), bridge graph t = 100, b <= 5 (GPU).  T90 = the
+smallest budget on the grid {64, 90, 128, 181, 256, ...} with mean
+recall@10 >= 0.9; every timed step searches all 10,000 queries at T90, k = 10.
+
+One step = one pass of the whole hot path over the 10,000-query batch with
+inputs resident in HBM.  L2 is flushed (256 MB write) before every timed step.
+`e2e` times the same step through the C ABI with queries in pinned host
+memory: host->device copy of the queries, search, device->host copy of ids
+and keys, all inside the timed region.
+
+--impl reference times the CPU oracle (oracle/) on the host cores, on a
+bounded sample of the same queries, T and index.
+
+Multi-GPU (torchrun): replicas only -- every rank builds its own index and
+searches its own 10,000 queries; value = all ranks' queries / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = 2
+T_GRID = [64, 90, 128, 181, 256, 362, 512, 724, 1024, 1448, 2048, 2896, 4096, 5792, 8192]
+K = 10
+METRIC = "queries/s at recall@10=0.9, persistent/served vs plain GPU search; p50/p99 ms"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=None, help="override reference count (smaller runs)")
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--T", type=int, default=None, help="skip the T90 sweep and use this budget")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------
+# distributed plumbing (replicas only: a barrier and a max, no data path)
+# --------------------------------------------------------------------------
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, ws, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def build_workload(args, torch, ann, datagen, log):
+    spec = dict(datagen.WORKLOADS[WORKLOAD])
+    N = args.N or spec["N"]
+    nq = args.nq or spec["nq"]
+    t0 = time.time()
+    Xh = datagen.references(WORKLOAD, N)
+    Qh = datagen.queries(WORKLOAD, nq)
+    log(f"data {N}x{spec['d']} + {nq} queries in {time.time() - t0:.1f}s")
+    X = torch.from_numpy(Xh).cuda()
+    Q = torch.from_numpy(Qh).cuda()
+    t0 = time.time()
+    G, _ = ann.ann_build_knn_graph(X, spec["R"])
+    torch.cuda.synchronize()
+    t_knn = time.time() - t0
+    t0 = time.time()
+    train_rows = datagen.training_rows(WORKLOAD, N)
+    train = X if train_rows is None else X[torch.from_numpy(train_rows).cuda()]
+    C = ann.ann_train_centers(train.contiguous(), spec["P"], spec["n"], 10,
+                              datagen.kmeans_init_rows(WORKLOAD, train.shape[0], spec["n"]))
+    t_km = time.time() - t0
+    t0 = time.time()
+    index = ann.Index.create(X, G, C, t=spec["t"], b=spec["b"])
+    t_bg = time.time() - t0
+    log(f"kNN graph {t_knn:.1f}s, k-means {t_km:.1f}s, bridge graph {t_bg:.1f}s")
+    info = index.info()
+    t0 = time.time()
+    gt_ids, gt_keys = ann.ann_exact_knn(X, Q, K)
+    torch.cuda.synchronize()
+    log(f"ground truth {time.time() - t0:.1f}s; index M={info['M']} alpha={info['alpha']:.3g}")
+    return dict(spec=spec, N=N, nq=nq, X=X, Q=Q, Xh=Xh, Qh=Qh, index=index, gt_ids=gt_ids, gt_keys=gt_keys,
+                info=info, G=G, C=C, build_s={"knn_graph": t_knn, "kmeans": t_km, "bridge_graph": t_bg})
+
+
+def recall_at_10(torch, ids, W):
+    """Mean r/k (Sec. 5.1), tie-tolerant: a returned id counts when its true
+    distance is <= the true 10th distance."""
+    X, Q, gt_keys = W["X"], W["Q"], W["gt_keys"]
+    kth = gt_keys[:, K - 1].to(torch.int64) & 0xFFFFFFFF
+    ids = ids[:, :K].long()
+    valid = ids >= 0
+    rows = X[ids.clamp(min=0)].to(torch.int32)                 # nq x k x d
+    diff = rows - Q[:, None, :].to(torch.int32)
+    dist = (diff * diff).sum(-1).to(torch.int64)
+    hit = valid & (dist <= kth[:, None])
+    return float(hit.sum().item()) / (K * ids.shape[0])
+
+
+def sweep_t90(args, torch, ann, W, log):
+    if args.T:
+        ids, _, _ = ann.ann_search_batch(W["index"], W["Q"], K, args.T, kmax=K, mode=1)
+        torch.cuda.synchronize()
+        r = recall_at_10(torch, ids, W)
+        return args.T, r, [(args.T, r)]
+    table = []
+    for T in T_GRID:
+        ids, _, st = ann.ann_search_batch(W["index"], W["Q"], K, T, kmax=K, mode=1)
+        torch.cuda.synchronize()
+        r = recall_at_10(torch, ids, W)
+        table.append((T, r))
+        log(f"T={T} recall@10={r:.4f}")
+        if r >= 0.9:
+            return T, r, table
+    return T_GRID[-1], table[-1][1], table
+
+
+# --------------------------------------------------------------------------
+# timing
+# --------------------------------------------------------------------------
+
+def time_steps(torch, fn, steps, warmup, flush_buf, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            flush_buf.fill_(1)                      # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    return times
+
+
+def served_run(torch, ann, W, T, datagen, log, duration_s=4.0, load_frac=0.8, plain_qps=1e5):
+    """Poisson arrivals of request batches (1-512 queries) into the server at
+    load_frac x the plain form's capacity; returns qps, p50/p99 latency (ms)."""
+    import ctypes
+    Qh = W["Qh"]
+    nreq = 4000
+    arrivals, sizes = datagen.poisson_requests(WORKLOAD, nreq, rate_qps=load_frac * plain_qps)
+    srv = ctypes.c_void_p()
+    ann.check(ann.lib.ann_server_create(W["index"].handle, 256 << 20, 4, ctypes.byref(srv)))
+    kk = np.full(512, K, np.int32)
+    TT = np.full(512, T, np.int32)
+    tickets = []
+    t_start = time.perf_counter()
+    at = 0
+    for i in range(nreq):
+        now = time.perf_counter() - t_start
+        if now > duration_s:
+            break
+        wait = arrivals[i] - now
+        if wait > 0:
+            time.sleep(wait)
+        n = int(sizes[i])
+        lo = at % (len(Qh) - 512)
+        at += n
+        q = np.ascontiguousarray(Qh[lo:lo + n])
+        tk = ctypes.c_uint64()
+        t_sub = time.perf_counter()
+        ann.check(ann.lib.ann_serve_submit(srv, q.ctypes.data, n, kk.ctypes.data, TT.ctypes.data, ctypes.byref(tk)))
+        tickets.append((tk.value, n, t_sub, lo))
+    ids = np.empty((512, K), np.int32)
+    lat = []
+    done_q = 0
+    t_last = t_start
+    pending = list(tickets)
+    while pending:
+        rest = []
+        for tk, n, t_sub, lo in pending:
+            rc = ann.lib.ann_serve_poll(srv, tk, ids.ctypes.data, None, None)
+            if rc == ann.ANN_OK:
+                now = time.perf_counter()
+                lat.append((now - t_sub) * 1e3)
+                done_q += n
+                t_last = max(t_last, now)
+            elif rc == ann.ANN_PENDING:
+                rest.append((tk, n, t_sub, lo))
+            else:
+                ann.check(rc)
+        pending = rest
+        if pending:
+            time.sleep(0.0002)
+    ann.lib.ann_server_destroy(srv)
+    span = t_last - t_start
+    return {"qps": done_q / span, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "requests": len(lat), "offered_qps": load_frac * plain_qps}
+
+
+# --------------------------------------------------------------------------
+# oracle (CPU) timing: bounded sample of the same workload
+# --------------------------------------------------------------------------
+
+def oracle_sample_qps(torch, ann, W, T, budget_s=15.0):
+    import oracle
+    index = W["index"]
+    info = index.info()
+    ids, refs = index.bridges()
+    lens = (refs >= 0).sum(1)
+    offs = np.zeros(len(ids) + 1, np.int64)
+    offs[1:] = np.cumsum(lens)
+    flat = refs[refs >= 0].astype(np.int32)
+    bg = {"bridges": ids, "offsets": offs, "refs": flat}
+    X = W["Xh"]
+    G = W["G_host"]
+    C = W["C_host"]
+    cores = os.cpu_count() or 1
+    Qh = W["Qh"]
+    n = cores
+    t0 = time.perf_counter()
+    oracle.search(X, G, C, bg, Qh[:n], K, T, kmax=K, nthreads=cores)
+    el = time.perf_counter() - t0
+    per = el / n
+    n2 = int(max(cores, min(len(Qh) - n, budget_s / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.search(X, G, C, bg, Qh[n:n + n2], K, T, kmax=K, nthreads=cores)
+    el = time.perf_counter() - t0
+    return n2 / el, cores, n2, el
+
+
+def index_host_copies(torch, ann, W):
+    """Graph and centers of the built index, on the host (for the CPU oracle)."""
+    W["G_host"] = W["G"].cpu().numpy()
+    W["C_host"] = W["C"].cpu().numpy()
+
+
+# --------------------------------------------------------------------------
+# algorithmic bytes of the search kernel (per step)
+# --------------------------------------------------------------------------
+
+def algorithmic_bytes(stats: np.ndarray, W) -> float:
+    """Bytes the method must move per step: vectors of discovered references,
+    kNN rows of expanded references, reference lists of popped bridges, the
+    prefix-index entries the bridge walks read, the query vectors and the
+    outputs; the part dictionaries once per step."""
+    spec, info = W["spec"], W["info"]
+    d, R, b = spec["d"], spec["R"], spec["b"]
+    disc, refp, brp, walks, nodes, leaves = (stats[:, i].astype(np.float64) for i in range(6))
+    per_q = disc * d + refp * R * 4 + brp * b * 4 + leaves * 4 + nodes * 0.125 + d + K * 8
+    centers = spec["P"] * spec["n"] * (d // spec["P"])
+    return float(per_q.sum() + centers)
+
+
+def main():
+    args = parse()
+    rank, ws, local = dist_init(args)
+
+    def log(msg):
+        if rank == 0:
+            print(f"[bench] {msg}", file=sys.stderr, flush=True)
+
+    if args.impl == "reference":
+        return reference_arm(args, rank, ws, log)
+
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1312_3062_gb300 import _build
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    barrier(ws)
+    from paper_1312_3062_gb300 import ann, datagen
+
+    W = build_workload(args, torch, ann, datagen, log)
+    T90, rec, table = sweep_t90(args, torch, ann, W, log)
+    log(f"T90={T90} recall@10={rec:.4f}")
+    nq = W["nq"]
+    index, Q = W["index"], W["Q"]
+    stream = torch.cuda.Stream()
+    out_ids = torch.empty((nq, K), dtype=torch.int32, device="cuda")
+    out_keys = torch.empty((nq, K), dtype=torch.int32, device="cuda")
+    out_st = torch.empty((nq,), dtype=torch.int32, device="cuda")
+    stats = torch.zeros((nq, ann.ANN_NSTATS), dtype=torch.int64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(mode):
+        ann.ann_search_batch(index, Q, K, T90, kmax=K, mode=mode, out_ids=out_ids, out_keys=out_keys,
+                             out_status=out_st, stream=stream)
+
+    # plain form
+    barrier(ws)
+    t_plain = time_steps(torch, lambda: step(0), args.steps, args.warmup, flush, stream)
+    # persistent form (CUDA graph replay), the headline
+    barrier(ws)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    t_pers = time_steps(torch, lambda: step(1), args.steps, args.warmup, flush, stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = clk.stop()
+    total_ms = max_over_ranks(sum(t_pers), ws, "cuda")
+    ms_per_step = total_ms / args.steps
+    value = nq * ws * args.steps / (total_ms / 1e3)
+    plain_qps = nq * args.steps / (sum(t_plain) / 1e3)
+    assert np.all(out_st.cpu().numpy() == 0)
+
+    # per-step counters for the algorithmic byte count (one extra untimed pass)
+    ann.ann_search_batch(index, Q, K, T90, kmax=K, mode=1, out_stats=stats, stream=stream)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+    alg_bytes = algorithmic_bytes(st, W)
+    # search-kernel time alone, measured on its stream (plain launch = one search kernel)
+    k_ms = statistics.mean(t_plain)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
+    if os.path.exists(prof):
+        pj = json.load(open(prof))
+        if pj.get("T") == T90 and pj.get("nq") == nq and pj.get("N") == W["N"]:
+            traffic = pj.get("dram_bytes_per_launch")
+
+    # end to end through the C ABI with pinned host buffers
+    q_host = torch.empty_like(Q, device="cpu").pin_memory()
+    q_host.copy_(Q.cpu())
+    ids_host = torch.empty((nq, K), dtype=torch.int32).pin_memory()
+    keys_host = torch.empty((nq, K), dtype=torch.int32).pin_memory()
+    q_dev = torch.empty_like(Q)
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            q_dev.copy_(q_host, non_blocking=True)
+            ann.ann_search_batch(index, q_dev, K, T90, kmax=K, mode=1, out_ids=out_ids, out_keys=out_keys,
+                                 out_status=out_st, stream=stream)
+            ids_host.copy_(out_ids, non_blocking=True)
+            keys_host.copy_(out_keys, non_blocking=True)
+
+    t_e2e = time_steps(torch, e2e_step, args.steps, args.warmup, flush, stream)
+    e2e_ms = max_over_ranks(sum(t_e2e), ws, "cuda")
+    e2e_value = nq * ws * args.steps / (e2e_ms / 1e3)
+
+    served = None
+    if not args.no_serve and rank == 0:
+        served = served_run(torch, ann, W, T90, datagen, log, plain_qps=plain_qps)
+
+    cpu_baseline = None
+    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+        index_host_copies(torch, ann, W)
+        qps, cores, n2, el = oracle_sample_qps(torch, ann, W, T90)
+        cpu_baseline = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                        "sample": f"{n2} queries of the same workload at T={T90}, k=10, one query per thread, "
+                                  f"{el:.1f}s; search only, on the index arrays the GPU built"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "queries/s",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_per_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "u8",
+            "data": "synthetic (seeded SIFT-shaped Gaussian mixture; the paper's datasets are not available)",
+            "config": {"workload": f"sift1m: N={W['N']} x 128 uint8, {nq} queries, kNN graph R=20, "
+                                   f"P=4 x n=256, b<=5, t=100",
+                       "T": T90, "k": K, "recall@10": rec, "mode": "persistent (CUDA graph, budget buckets)",
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "recall_vs_T": table},
+            "plain": {"qps": plain_qps, "ms_per_step": statistics.mean(t_plain)},
+            "persistent": {"qps": value / ws, "ms_per_step": ms_per_step},
+            "served": served,
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.numel()),
+                    "d2h_bytes_per_step": int(nq * K * 8)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "search_kernel<u8> (plain launch)",
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "cpu_baseline": cpu_baseline,
+            "clocks": clocks,
+            "gpu_launches": args.steps * 2,
+            "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
+                                                   "bytes_bridges")}, "build_s": W["build_s"]},
+        }
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+def reference_arm(args, rank, ws, log):
+    """The CPU oracle, as it stands, on the machine's host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import torch
+    from paper_1312_3062_gb300 import _build
+    _build.build()
+    import oracle
+    oracle.build()
+    from paper_1312_3062_gb300 import ann, datagen
+    torch.cuda.set_device(0)
+    W = build_workload(args, torch, ann, datagen, log)
+    T90, rec, _ = sweep_t90(args, torch, ann, W, log)
+    index_host_copies(torch, ann, W)
+    cores = os.cpu_count() or 1
+    ids, refs = W["index"].bridges()
+    lens = (refs >= 0).sum(1)
+    offs = np.zeros(len(ids) + 1, np.int64)
+    offs[1:] = np.cumsum(lens)
+    bg = {"bridges": ids, "offsets": offs, "refs": refs[refs >= 0].astype(np.int32)}
+    per_step = max(cores, 2 * cores)
+    Qh = W["Qh"]
+    for i in range(args.warmup):
+        oracle.search(W["Xh"], W["G_host"], W["C_host"], bg, Qh[:cores], K, T90, kmax=K, nthreads=cores)
+    t0 = time.perf_counter()
+    done = 0
+    for s in range(args.steps):
+        lo = (s * per_step) % (len(Qh) - per_step)
+        oracle.search(W["Xh"], W["G_host"], W["C_host"], bg, Qh[lo:lo + per_step], K, T90, kmax=K,
+                      nthreads=cores)
+        done += per_step
+    el = time.perf_counter() - t0
+    v = done / el
+    line = {"metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"sift1m: N={W['N']} x 128 uint8, {per_step} queries per step (sample of "
+                                   f"{W['nq']}), R=20, P=4 x n=256, b<=5, t=100", "T": T90, "k": K},
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{per_step} queries per step, one query per thread"},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

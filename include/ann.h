@@ -1,0 +1,202 @@
+/*
+ * ann.h -- C ABI of the GB300 (sm_103a) library for approximate nearest
+ * neighbour search over the augmented neighbourhood graph of
+ * "Fast Neighborhood Graph Search using Cartesian Concatenation"
+ * (Wang, Wang, Zeng, Tu, Gan, Li; arXiv:1312.3062).
+ *
+ * Problem (Sec. 2): given reference vectors X (N x d, Euclidean), a query q,
+ * a budget T (number of reference vectors examined: time-constrained search)
+ * and k, return k reference ids with their distances.  The index (Sec. 4.1)
+ * is an exact R-NN neighbourhood graph over X plus a bridge graph between the
+ * Cartesian concatenation of P per-part center sets and X.  The search is
+ * Algorithm 1 (Sec. 4.2).
+ *
+ * Conventions for every entry point:
+ *  - Every call returns an ann_status; no C++ exception crosses the ABI.
+ *    On failure ann_last_error() returns a thread-local message.
+ *  - "device" pointers are CUDA device (or managed) pointers on the current
+ *    device; "host" pointers are ordinary CPU memory.  The library never
+ *    frees caller memory; handles own their own device memory.
+ *  - Keys are SQUARED Euclidean distances: uint32 for ANN_U8 data (exact),
+ *    float32 for ANN_F32 data (the float32 nearest to the exact value).
+ *    Ties are broken by the smaller id everywhere.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *    take a stream are asynchronous unless stated otherwise; device-side
+ *    failures are reported per query in out_status, never by a trap.
+ *  - Limits: 2 <= P <= 4, n <= 256, d % P == 0, d % 16 == 0 (u8) or
+ *    d % 4 == 0 (f32), n^P <= 2^32, R <= 32, b <= 8, k <= 128, T <= 8192.
+ */
+#ifndef ANN_H
+#define ANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { ANN_U8 = 0, ANN_F32 = 1 } ann_dtype;
+
+typedef enum {
+    ANN_OK = 0,
+    ANN_PENDING = 1,       /* serve_poll: request still running */
+    ANN_ERR_ARG = -1,      /* invalid argument (message says which) */
+    ANN_ERR_OOM = -2,      /* device allocation failed / request never admissible */
+    ANN_ERR_CAPACITY = -3, /* a per-query on-chip capacity was exceeded */
+    ANN_ERR_TIMEOUT = -4,  /* a bounded device wait gave up */
+    ANN_ERR_CUDA = -5,     /* a CUDA runtime call failed */
+    ANN_ERR_FORMAT = -6    /* index file malformed */
+} ann_status;
+
+typedef struct ann_index ann_index;   /* opaque; owns device copies of all index arrays */
+typedef struct ann_server ann_server; /* opaque; owns the serving loop, queues and scratch */
+
+/* Thread-local description of the last failure in this thread. */
+const char *ann_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Index construction                                                        */
+/* ------------------------------------------------------------------------ */
+
+/* Exact k nearest neighbours by linear scan (Sec. 2; the ground truth of
+ * Sec. 5.1).  refs: device, N*d elements of dtype, row-major.  queries:
+ * device, nq*d.  For each query, the k rows of refs with the smallest
+ * (key, id), ascending.  exclude_self=1 requires queries == refs (nq == N)
+ * and skips row i for query i: this is the exact R-NN neighbourhood graph of
+ * Sec. 3.1 / Sec. 4.1.  Rows with fewer than k candidates are padded with
+ * id -1 / key UINT32_MAX (u8) or +inf (f32).  out_ids: device int32[nq*k];
+ * out_keys: device, optional (NULL), nq*k keys.  k <= 32. */
+int ann_exact_knn(const void *refs, int64_t N, const void *queries, int64_t nq, int dtype,
+                  int32_t d, int32_t k, int32_t exclude_self, int32_t *out_ids, void *out_keys,
+                  void *stream);
+
+/* Exact R-NN neighbourhood graph of data (Sec. 3.1, Sec. 4.1): same as
+ * ann_exact_knn(data, N, data, N, dtype, d, R, 1, ...). */
+int ann_build_knn_graph(const void *data, int dtype, int64_t N, int32_t d, int32_t R,
+                        int32_t *out_ids, void *out_keys, void *stream);
+
+/* Per-part dictionaries for the bridge vectors (Sec. 4.1, "Computing bridge
+ * vectors": product quantization, i.e. k-means on each of the P contiguous
+ * parts of d/P dims).  Lloyd's algorithm in fp64: center j of every part
+ * starts at training row init_rows[j] (host int64[n], distinct); assignment
+ * ties go to the lower center; an empty cluster keeps its previous center.
+ * train: device, ntrain*d elements.  out_centers: device, P*n*(d/P)
+ * elements of dtype (u8: rounded half-to-even and clipped to [0,255]);
+ * out_centers_f64: device, optional, the unrounded P*n*(d/P) doubles.
+ * Synchronous. */
+int ann_train_centers(const void *train, int dtype, int64_t ntrain, int32_t d, int32_t P,
+                      int32_t n, int32_t iters, const int64_t *init_rows, void *out_centers,
+                      double *out_centers_f64, void *stream);
+
+/* Everything an index is made of.  data/graph/centers: device pointers (they
+ * are copied).  If bridge_ids is NULL the bridge graph is built on the GPU
+ * (Sec. 4.1: for each reference vector its top-t bridge vectors; for each
+ * bridge vector the b nearest of those references).  Otherwise the caller
+ * supplies it on the host: M ascending bridge ids (mixed radix of center ids,
+ * part 0 most significant), CSR offsets int64[M+1] and reference ids, each
+ * list ascending by (key to the bridge, id) and at most b long. */
+typedef struct {
+    int32_t dtype;
+    int64_t N;
+    int32_t d, R, P, n, t, b;
+    const void *data;         /* device, N*d */
+    const int32_t *graph;     /* device, N*R (-1 = no neighbour) */
+    const void *centers;      /* device, P*n*(d/P) */
+    int64_t M;                /* host bridge graph (optional) */
+    const uint64_t *bridge_ids;
+    const int64_t *bridge_offsets;
+    const int32_t *bridge_refs;
+} ann_index_desc;
+
+/* Create an index on the current device.  Synchronous. */
+int ann_index_create(const ann_index_desc *desc, ann_index **out);
+
+/* Load an index written by ann_index_save onto `device` (-1 = current). */
+int ann_index_load(const char *path, int device, ann_index **out);
+int ann_index_save(const ann_index *index, const char *path);
+int ann_index_free(ann_index *index);
+
+/* Index statistics (Table 1: #reference and alpha). */
+typedef struct {
+    int64_t N, M;             /* references; non-empty bridge vectors */
+    int32_t d, R, P, n, b, dtype;
+    int64_t bridged_refs;     /* distinct references attached to some bridge */
+    double alpha;             /* bridged_refs / n^P */
+    int64_t bytes_vectors, bytes_graph, bytes_bridges;
+} ann_index_info;
+int ann_index_get_info(const ann_index *index, ann_index_info *out);
+
+/* Copy the bridge graph back to the host: bridge ids (uint64[M], ascending)
+ * and refs (int32[M*b], each list padded with -1). */
+int ann_index_get_bridges(const ann_index *index, uint64_t *ids, int32_t *refs);
+
+/* ------------------------------------------------------------------------ */
+/* Search: Algorithm 1 (Sec. 4.2)                                            */
+/* ------------------------------------------------------------------------ */
+
+enum { ANN_MODE_PLAIN = 0, ANN_MODE_PERSISTENT = 1 };
+
+/* Per-query counters (out_stats, int64 each). */
+enum {
+    ANN_STAT_DISCOVERED = 0, /* t: reference vectors discovered (= distances computed) */
+    ANN_STAT_REF_POPS,       /* reference vectors popped and expanded */
+    ANN_STAT_BRIDGE_POPS,    /* non-empty bridge vectors popped */
+    ANN_STAT_WALKS,          /* bridge-index walks (one per batch of bridges) */
+    ANN_STAT_WALK_NODES,     /* prefix nodes read by those walks */
+    ANN_STAT_WALK_LEAVES,    /* leaf entries read by those walks */
+    ANN_STAT_MAX_Q,          /* largest main-queue length */
+    ANN_STAT_RESERVED,
+    ANN_NSTATS
+};
+
+/* Batched search.  queries: device, nq*d elements of the index dtype.
+ * k, T: device int32[nq] per-query result counts and budgets, or NULL to use
+ * k_all / T_all for every query.  kmax >= every k.  Outputs (device,
+ * caller-owned): out_ids int32[nq*kmax] ascending by (key, id), padded with
+ * -1; out_keys (optional) nq*kmax keys padded with UINT32_MAX / +inf;
+ * out_status (optional) int32[nq] with ANN_OK or ANN_ERR_CAPACITY;
+ * out_stats (optional) int64[nq*ANN_NSTATS].
+ * mode ANN_MODE_PLAIN: kernels launched for this batch on `stream`.
+ * mode ANN_MODE_PERSISTENT: queries are bucketed by budget and run by one
+ * persistent kernel per bucket pulling work from a device queue, the whole
+ * batch replayed as a CUDA graph captured once per (index, shape).
+ * Results are identical in both modes.  Asynchronous. */
+int ann_search_batch(const ann_index *index, const void *queries, int64_t nq, const int32_t *k,
+                     const int32_t *T, int32_t k_all, int32_t T_all, int32_t kmax, int32_t mode,
+                     int32_t *out_ids, void *out_keys, int32_t *out_status, int64_t *out_stats,
+                     void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching with memory-based admission                  */
+/* ------------------------------------------------------------------------ */
+
+/* A server keeps the index resident, owns a pool of scratch_bytes of device
+ * memory and a host thread that admits submitted requests whenever their
+ * scratch fits, launching them on its own streams so requests overlap on the
+ * GPU.  Results are identical to ann_search_batch for the same queries. */
+int ann_server_create(const ann_index *index, size_t scratch_bytes, int32_t max_streams,
+                      ann_server **out);
+int ann_server_destroy(ann_server *server);
+
+/* Submit nq queries (host memory, copied at once) with per-query k, T (host
+ * int32[nq]).  *ticket identifies the request.  ANN_ERR_OOM if the request
+ * could never fit in the scratch pool. */
+int ann_serve_submit(ann_server *server, const void *host_queries, int32_t nq, const int32_t *k,
+                     const int32_t *T, uint64_t *ticket);
+
+/* Non-blocking.  ANN_PENDING while running; ANN_OK once done, after copying
+ * ids (int32[nq*kmax_req]), keys (optional) and status (optional, int32[nq])
+ * to the host buffers, where kmax_req is the request's largest k.  The
+ * ticket is released by the successful poll. */
+int ann_serve_poll(ann_server *server, uint64_t ticket, int32_t *host_ids, void *host_keys,
+                   int32_t *host_status);
+
+/* Submit-to-completion latency in seconds of a finished (polled) ticket's
+ * request, measured by the server; -1 if unknown. */
+double ann_serve_latency(ann_server *server, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANN_H */

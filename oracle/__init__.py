@@ -55,13 +55,13 @@ def _load():
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i64, i32 = ctypes.c_int64, ctypes.c_int
-            lib.oracle_exact_knn.argtypes = [P, i64, P, i64, i32, i32, i32, i32, P, P]
+            lib.oracle_exact_knn.argtypes = [P, i64, P, i64, i32, i32, i32, i32, P, P, i32]
             lib.oracle_exact_knn.restype = None
             lib.oracle_kmeans.argtypes = [P, i64, i32, i32, i32, i32, i32, P, P]
             lib.oracle_kmeans.restype = None
             lib.oracle_multiseq.argtypes = [P, i32, i32, i32, i64, P, P, P, P]
             lib.oracle_multiseq.restype = i64
-            lib.oracle_bridge_graph.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, P, P, P]
+            lib.oracle_bridge_graph.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, P, P, P, i32]
             lib.oracle_bridge_graph.restype = i64
             lib.oracle_search.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P, P, P,
                                           i64, P, P, i32, P, P, P, P, i32, i32]
@@ -84,8 +84,13 @@ def _dtype_code(X: np.ndarray) -> int:
     raise TypeError(f"unsupported dtype {X.dtype}")
 
 
-def exact_knn(X: np.ndarray, Qs: np.ndarray, k: int, exclude_self: bool = False):
-    """Linear-scan k-NN by (squared distance, id); pads with -1 / +inf."""
+def _threads(n):
+    return int(n) if n else (os.cpu_count() or 1)
+
+
+def exact_knn(X: np.ndarray, Qs: np.ndarray, k: int, exclude_self: bool = False, nthreads: int = 0):
+    """Linear-scan k-NN by (squared distance, id); pads with -1 / +inf.
+    Query rows are independent; nthreads (0 = all cores) only splits them."""
     lib = _load()
     X = np.ascontiguousarray(X)
     Qs = np.ascontiguousarray(Qs)
@@ -94,13 +99,13 @@ def exact_knn(X: np.ndarray, Qs: np.ndarray, k: int, exclude_self: bool = False)
     ids = np.empty((nq, k), np.int32)
     keys = np.empty((nq, k), np.float64)
     lib.oracle_exact_knn(_ptr(X), X.shape[0], _ptr(Qs), nq, X.shape[1], _dtype_code(X), k,
-                         int(exclude_self), _ptr(ids), _ptr(keys))
+                         int(exclude_self), _ptr(ids), _ptr(keys), _threads(nthreads))
     return ids, keys
 
 
-def knn_graph(X: np.ndarray, R: int):
+def knn_graph(X: np.ndarray, R: int, nthreads: int = 0):
     """Exact R-NN graph: each row ascending by (key, id), self excluded."""
-    return exact_knn(X, X, R, exclude_self=True)
+    return exact_knn(X, X, R, exclude_self=True, nthreads=nthreads)
 
 
 def kmeans(X: np.ndarray, P: int, n: int, iters: int, init_rows: np.ndarray) -> np.ndarray:
@@ -139,8 +144,9 @@ def multiseq(part_keys: np.ndarray, dtype, m: int):
     return keys[:got], ids[:got], ranks[:got], {"max_frontier": int(st[0]), "pushes": int(st[1])}
 
 
-def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int):
-    """Bridge graph: dict with ascending 'bridges' (uint64), CSR 'offsets', 'refs', 'keys'."""
+def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int, nthreads: int = 0):
+    """Bridge graph: dict with ascending 'bridges' (uint64), CSR 'offsets', 'refs', 'keys'.
+    References are independent in the top-t step; nthreads (0 = all cores) splits them."""
     lib = _load()
     X = np.ascontiguousarray(X)
     centers = np.ascontiguousarray(centers)
@@ -154,7 +160,7 @@ def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int):
     refs = np.empty(cap, np.int32)
     keys = np.empty(cap, np.float64)
     M = lib.oracle_bridge_graph(_ptr(X), N, d, _dtype_code(X), P, n, _ptr(centers), t, b,
-                                _ptr(bridges), _ptr(offsets), _ptr(refs), _ptr(keys))
+                                _ptr(bridges), _ptr(offsets), _ptr(refs), _ptr(keys), _threads(nthreads))
     nnz = int(offsets[M])
     return {"bridges": bridges[:M].copy(), "offsets": offsets[:M + 1].copy(),
             "refs": refs[:nnz].copy(), "keys": keys[:nnz].copy(), "P": P, "n": n}

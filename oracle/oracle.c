@@ -16,7 +16,8 @@
  *  - float32 data: a key is computed in fp64 and then rounded to the nearest
  *    float32; every comparison is taken on that float32 value (the kernel's
  *    precision), so both implementations order candidates identically.
- *    A bridge key is the float32 sum of the part keys added left to right.
+ *    A bridge key is the float32 sum (D0 + D1) + (D2 + D3 + ...) of the part
+ *    keys, the second group added left to right.
  *  - Main queue order: (key, kind, id), kind ref = 0 < bridge = 1.
  *  - Result set: the k smallest by (key, id), returned ascending, padded with
  *    id -1 / key +inf when fewer than k points were discovered.
@@ -70,16 +71,23 @@ static const void *row_ptr(const void *base, int64_t row, int len, int dtype) {
     return (const float *)base + row * (int64_t)len;
 }
 
-/* Bridge key from P part keys (Sec. 4.2: dist^2(q, y) = sum_p dist^2(q^p, y^p)). */
+/* Bridge key from P part keys (Sec. 4.2: dist^2(q, y) = sum_p dist^2(q^p, y^p)).
+   For float32 the sum is taken in float32 with a fixed grouping: the first
+   two parts, plus the remaining parts added left to right, i.e.
+   (D0 + D1) + ((D2 + D3) + ...).  Any fixed grouping is monotone in every
+   part key; this one is fixed here so both implementations round alike. */
 static double bridge_key(const double *part_keys, int P, int dtype) {
     if (dtype == DT_U8) {
         double s = 0.0; /* integers far below 2^53: exact */
         for (int p = 0; p < P; p++) s += part_keys[p];
         return s;
     } else {
-        float s = (float)part_keys[0];
-        for (int p = 1; p < P; p++) s = s + (float)part_keys[p];
-        return (double)s;
+        if (P == 1) return (double)(float)part_keys[0];
+        float a = (float)part_keys[0] + (float)part_keys[1];
+        if (P == 2) return (double)a;
+        float b = (float)part_keys[2];
+        for (int p = 3; p < P; p++) b = b + (float)part_keys[p];
+        return (double)(a + b);
     }
 }
 
@@ -117,26 +125,60 @@ static void topk_insert(double *keys, int64_t *ids, int *len, int cap, double ke
 
 /* For each query row i of Qs, the k nearest rows of X by (key, id).  When
    exclude_self is set, Qs must be X and row i is skipped for query i.
-   Rows with fewer than k candidates are padded with id -1 / key +inf. */
-void oracle_exact_knn(const void *X, int64_t N, const void *Qs, int64_t nq, int d, int dtype,
-                      int k, int exclude_self, int32_t *out_ids, double *out_keys) {
-    double *keys = (double *)malloc(sizeof(double) * (size_t)k);
-    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)k);
-    for (int64_t i = 0; i < nq; i++) {
-        int len = 0;
-        const void *q = row_ptr(Qs, i, d, dtype);
-        for (int64_t j = 0; j < N; j++) {
-            if (exclude_self && j == i) continue;
-            double key = sqdist(q, row_ptr(X, j, d, dtype), d, dtype);
-            topk_insert(keys, ids, &len, k, key, j);
-        }
-        for (int r = 0; r < k; r++) {
-            out_ids[i * k + r] = r < len ? (int32_t)ids[r] : -1;
-            out_keys[i * k + r] = r < len ? keys[r] : INFINITY;
-        }
+   Rows with fewer than k candidates are padded with id -1 / key +inf.
+   Query rows are independent; nthreads > 1 splits them across threads. */
+typedef struct {
+    const void *X, *Qs;
+    int64_t N, nq;
+    int d, dtype, k, exclude_self;
+    int32_t *out_ids;
+    double *out_keys;
+    int64_t next;
+    pthread_mutex_t mu;
+} knn_job_t;
+
+static void knn_rows(knn_job_t *j, int64_t i) {
+    double *keys = (double *)malloc(sizeof(double) * (size_t)j->k);
+    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)j->k);
+    int len = 0;
+    const void *q = row_ptr(j->Qs, i, j->d, j->dtype);
+    for (int64_t r = 0; r < j->N; r++) {
+        if (j->exclude_self && r == i) continue;
+        double key = sqdist(q, row_ptr(j->X, r, j->d, j->dtype), j->d, j->dtype);
+        topk_insert(keys, ids, &len, j->k, key, r);
+    }
+    for (int r = 0; r < j->k; r++) {
+        j->out_ids[i * j->k + r] = r < len ? (int32_t)ids[r] : -1;
+        j->out_keys[i * j->k + r] = r < len ? keys[r] : INFINITY;
     }
     free(keys);
     free(ids);
+}
+
+static void *knn_worker(void *arg) {
+    knn_job_t *j = (knn_job_t *)arg;
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t i = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (i >= j->nq) break;
+        knn_rows(j, i);
+    }
+    return NULL;
+}
+
+void oracle_exact_knn(const void *X, int64_t N, const void *Qs, int64_t nq, int d, int dtype,
+                      int k, int exclude_self, int32_t *out_ids, double *out_keys, int nthreads) {
+    knn_job_t job = {X, Qs, N, nq, d, dtype, k, exclude_self, out_ids, out_keys, 0,
+                     PTHREAD_MUTEX_INITIALIZER};
+    if (nthreads <= 1) {
+        knn_worker(&job);
+        return;
+    }
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, knn_worker, &job);
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    free(th);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -490,26 +532,61 @@ static int triple_cmp(const void *a, const void *b) {
      offsets[M+1]   CSR offsets into refs/keys,
      refs, keys     the kept references and their keys to the bridge.
    Returns M. */
-int64_t oracle_bridge_graph(const void *X, int64_t N, int d, int dtype, int P, int n,
-                            const void *centers, int t, int b, uint64_t *bridges,
-                            int64_t *offsets, int32_t *refs, double *keys) {
-    triple_t *all = (triple_t *)malloc(sizeof(triple_t) * (size_t)N * (size_t)t);
-    int64_t cnt = 0;
-    tables_t tb = tables_alloc(P, n);
-    for (int64_t i = 0; i < N; i++) {
-        tables_build(&tb, row_ptr(X, i, d, dtype), d, dtype, P, n, centers);
+typedef struct {
+    const void *X, *centers;
+    int64_t N;
+    int d, dtype, P, n, t;
+    triple_t *all;
+    int64_t *count; /* per reference: how many of its t slots are filled */
+    int64_t next;
+    pthread_mutex_t mu;
+} bg_job_t;
+
+static void *bg_worker(void *arg) {
+    bg_job_t *j = (bg_job_t *)arg;
+    tables_t tb = tables_alloc(j->P, j->n);
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t i = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (i >= j->N) break;
+        tables_build(&tb, row_ptr(j->X, i, j->d, j->dtype), j->d, j->dtype, j->P, j->n, j->centers);
         mseq_t ms;
         ms_init(&ms, &tb);
         ms_item it;
-        for (int j = 0; j < t && ms_next(&ms, &it); j++) {
-            all[cnt].bridge = bridge_id_of(&tb, it.r);
-            all[cnt].key = it.key;
-            all[cnt].ref = (int32_t)i;
-            cnt++;
+        int64_t c = 0;
+        for (int s = 0; s < j->t && ms_next(&ms, &it); s++) {
+            triple_t *o = &j->all[i * j->t + c++];
+            o->bridge = bridge_id_of(&tb, it.r);
+            o->key = it.key;
+            o->ref = (int32_t)i;
         }
+        j->count[i] = c;
         ms_free(&ms);
     }
     tables_free(&tb);
+    return NULL;
+}
+
+int64_t oracle_bridge_graph(const void *X, int64_t N, int d, int dtype, int P, int n,
+                            const void *centers, int t, int b, uint64_t *bridges,
+                            int64_t *offsets, int32_t *refs, double *keys, int nthreads) {
+    triple_t *all = (triple_t *)malloc(sizeof(triple_t) * (size_t)N * (size_t)t);
+    int64_t *count = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    bg_job_t job = {X, centers, N, d, dtype, P, n, t, all, count, 0, PTHREAD_MUTEX_INITIALIZER};
+    if (nthreads <= 1) {
+        bg_worker(&job);
+    } else {
+        pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+        for (int q = 0; q < nthreads; q++) pthread_create(&th[q], NULL, bg_worker, &job);
+        for (int q = 0; q < nthreads; q++) pthread_join(th[q], NULL);
+        free(th);
+    }
+    /* compact (references with fewer than t bridges only when n^P < t) */
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < N; i++)
+        for (int64_t c = 0; c < count[i]; c++) all[cnt++] = all[i * t + c];
+    free(count);
     qsort(all, (size_t)cnt, sizeof(triple_t), triple_cmp);
     int64_t M = 0, out = 0;
     for (int64_t s = 0; s < cnt;) {

@@ -1,0 +1,84 @@
+// ann_internal.cuh -- shared internals of the sm_103a library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ann.h"
+
+namespace ann {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define ANN_CUDA(call)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::ann::cuda_fail(_e, #call);       \
+    } while (0)
+
+#define ANN_ARG(cond, msg)                                               \
+    do {                                                                 \
+        if (!(cond)) return ::ann::fail(ANN_ERR_ARG, msg);               \
+    } while (0)
+
+constexpr int kMaxP = 4;
+constexpr int kMaxN = 256;
+constexpr int kMaxR = 32;
+constexpr int kMaxB = 8;
+constexpr int kMaxK = 128;
+constexpr int kMaxT = 8192;
+
+// ---------------------------------------------------------------------------
+// index (device side)
+// ---------------------------------------------------------------------------
+// Bridge index layout.  Non-empty bridge vectors are kept sorted by bridge id
+// (mixed radix of center ids, part 0 most significant).  The first PA parts
+// (PA = min(2, P-1)) form the prefix "A" node a = c0*n + c1 (or c0), the
+// remaining parts the suffix, packed as mixed radix `leaf`.  For every prefix
+// node: a presence bit (bmA) and a CSR range [offA[a], offA[a+1]) of
+// bridges; each bridge has b reference slots (-1 padded).
+struct DevIndex {
+    int dtype;
+    int64_t N;
+    int d, R, P, n, b, t;
+    int PA;
+    int64_t nA;          // n^PA
+    int64_t M;           // non-empty bridges
+    const void *X;       // N*d
+    const int32_t *G;    // N*R
+    const void *C;       // P*n*(d/P)
+    const uint32_t *bmA; // ceil(nA/32) words
+    const uint32_t *offA;// nA+1
+    const uint32_t *leaf;// M
+    const int32_t *brefs;// M*b
+};
+
+}  // namespace ann
+
+struct ann_index {
+    int device;
+    ann::DevIndex dev;
+    // owned allocations
+    void *X, *C;
+    int32_t *G;
+    uint32_t *bmA, *offA, *leaf;
+    int32_t *brefs;
+    int64_t bridged_refs;
+    // cached persistent-mode plans (see ann_search.cu)
+    void *plans;
+};
+
+namespace ann {
+// implemented in ann_search.cu
+void free_plans(ann_index *ix);
+// implemented in ann_index.cu
+int build_bridge_index_from_host(ann_index *ix, int64_t M, const uint64_t *ids,
+                                 const int64_t *offsets, const int32_t *refs);
+}  // namespace ann

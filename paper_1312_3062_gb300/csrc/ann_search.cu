@@ -1,0 +1,956 @@
+// ann_search.cu -- Algorithm 1 (Sec. 4.2) of arXiv:1312.3062 on sm_103a.
+//
+// One warp runs one query from start to finish:
+//   1. part tables  D_p[c] = ||q^p - c_p||^2           (Sec. 4.2, first step)
+//   2. per-part sort by (key, center id) -> ranks        (Sec. 4.2)
+//   3. the main loop of Algorithm 1: a shared min-queue of reference vectors
+//      and the current bridge vector, the visited set (Color), the result set
+//      R and the exact budget T.
+// Bridge vectors are produced in the order of the multi-sequence algorithm
+// (Sec. 3.3): ascending (bridge key, rank tuple).  A popped bridge vector
+// with an empty list discovers nothing and only makes the next one current,
+// so Algorithm 1's result depends only on the order of the NON-EMPTY bridges.
+// The GPU therefore generates exactly that subsequence, in batches: a walk of
+// the prefix index of non-empty bridges emits every bridge whose
+// (key, ranks) lies in a window (lo, hi], and the batch is sorted.  The
+// window grows geometrically; an overfull window is halved.
+//
+// All per-query state lives in the warp's slice of shared memory; no device
+// trap or unbounded wait exists on this path.  Keys are squared distances:
+// exact uint32 for uint8 data; for float32 data the float32 nearest to the
+// exact value (double-float accumulation, then one rounding).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "ann_device.cuh"
+#include "ann_internal.cuh"
+
+namespace ann {
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of one warp
+// ---------------------------------------------------------------------------
+struct WarpLayout {
+    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, misc, total;
+    uint32_t heap_cap, hash_log, bcap, ncap;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
+                                                  int kmax, int bcap) {
+    WarpLayout L;
+    uint32_t o = 0;
+    L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
+    L.tabD = o;   o = align_up(o + 4u * P * n, 16);
+    L.rank = o;   o = align_up(o + (uint32_t)P * n, 16);
+    L.sk = o;     o = align_up(o + 4u * PA * n, 16);
+    L.sc = o;     o = align_up(o + (uint32_t)PA * n, 16);
+    uint32_t lpn = 1;
+    while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
+    uint32_t hc = (uint32_t)capT > lpn ? (uint32_t)capT : lpn;
+    L.heap_cap = hc;
+    L.heap = o;   o = align_up(o + 8u * hc, 16);
+    uint32_t hl = 5;
+    while ((1u << hl) < 2u * (uint32_t)capT) hl++;
+    L.hash_log = hl;
+    L.hash = o;   o = align_up(o + 4u * (1u << hl), 16);
+    L.rbuf = o;   o = align_up(o + 8u * kmax, 16);
+    L.bcap = (uint32_t)bcap;
+    L.bkey = o;   o = align_up(o + 8u * bcap, 16);
+    L.bidx = o;   o = align_up(o + 4u * bcap, 16);
+    L.pref = o;   o = align_up(o + 4u * (n + 1), 16);
+    L.ncap = 128;
+    L.nodes = o;  o = align_up(o + 16u * L.ncap, 16);
+    L.cand = o;   o = align_up(o + 4u * 32, 16);
+    L.ckey = o;   o = align_up(o + 4u * 32, 16);
+    L.misc = o;   o = align_up(o + 16u * 4, 16);
+    L.total = o;
+    return L;
+}
+
+struct SearchArgs {
+    DevIndex ix;
+    const void *queries;
+    int64_t nq;
+    const int32_t *k;
+    const int32_t *T;
+    int32_t k_all, T_all, kmax;
+    int32_t *out_ids;
+    void *out_keys;
+    int32_t *out_status;
+    int64_t *out_stats;
+    // query selection: list (nullable) of query indices; count from *list_count if non-null
+    const int32_t *list;
+    const int32_t *list_count;
+    int64_t list_len;
+    // persistent mode: work ticket counter (nullable)
+    int32_t *ticket;
+    int capT;
+    int bcap;
+    WarpLayout L;
+};
+
+// ---------------------------------------------------------------------------
+// visited set: open addressing over ids (slot = id + 1, 0 = empty)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t hslot(uint32_t x, uint32_t log) {
+    return (x * 2654435761u) >> (32 - log);
+}
+__device__ __forceinline__ bool hash_has(const uint32_t *H, uint32_t log, uint32_t x) {
+    uint32_t mask = (1u << log) - 1, h = hslot(x, log);
+    for (uint32_t i = 0; i <= mask; i++) {
+        uint32_t v = H[h];
+        if (v == x + 1) return true;
+        if (v == 0) return false;
+        h = (h + 1) & mask;
+    }
+    return false;
+}
+__device__ __forceinline__ void hash_add(uint32_t *H, uint32_t log, uint32_t x) {
+    uint32_t mask = (1u << log) - 1, h = hslot(x, log);
+    for (uint32_t i = 0; i <= mask; i++) {
+        uint32_t prev = atomicCAS(&H[h], 0u, x + 1);
+        if (prev == 0 || prev == x + 1) return;
+        h = (h + 1) & mask;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// main-queue heap of reference entries (key << 32 | id), run by lane 0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void heap_push(uint64_t *h, uint32_t &sz, uint64_t v) {
+    uint32_t i = sz++;
+    while (i > 0) {
+        uint32_t p = (i - 1) >> 1;
+        uint64_t pv = h[p];
+        if (pv <= v) break;
+        h[i] = pv;
+        i = p;
+    }
+    h[i] = v;
+}
+__device__ __forceinline__ uint64_t heap_pop(uint64_t *h, uint32_t &sz) {
+    uint64_t top = h[0];
+    uint64_t v = h[--sz];
+    uint32_t i = 0;
+    for (;;) {
+        uint32_t l = 2 * i + 1;
+        if (l >= sz) break;
+        uint32_t r = l + 1;
+        uint32_t c = (r < sz && h[r] < h[l]) ? r : l;
+        if (h[c] >= v) break;
+        h[i] = h[c];
+        i = c;
+    }
+    if (sz > 0) h[i] = v;
+    return top;
+}
+
+// ---------------------------------------------------------------------------
+// distance of the candidates listed in cand[0..m) to the query (keys -> ckey)
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ void cand_distances(const DevIndex &ix, const uint8_t *qbytes, const uint32_t *cand, int m,
+                               uint32_t *ckey) {
+    const int lane = lane_id();
+    const int vb = ix.d * (DT == ANN_U8 ? 1 : 4);  // bytes per vector
+    const int nc = vb >> 4;                          // 16-byte chunks
+    int G = 1;
+    while (G * 2 <= nc && G * 2 <= 32) G *= 2;
+    const int per_round = 32 / G;
+    const int lig = lane & (G - 1);
+    const int grp = lane / G;
+    for (int base = 0; base < m; base += per_round) {
+        int j = base + grp;
+        bool act = j < m;
+        uint32_t acc = 0;
+        float hi = 0.f, lo = 0.f;
+        if (act) {
+            const uint4 *row = (const uint4 *)((const uint8_t *)ix.X + (int64_t)cand[j] * vb);
+            const uint4 *qv = (const uint4 *)qbytes;
+            for (int c = lig; c < nc; c += G) {
+                uint4 a = __ldg(row + c);
+                uint4 b = qv[c];
+                if (DT == ANN_U8) {
+                    uint32_t d0 = __vabsdiffu4(a.x, b.x), d1 = __vabsdiffu4(a.y, b.y);
+                    uint32_t d2 = __vabsdiffu4(a.z, b.z), d3 = __vabsdiffu4(a.w, b.w);
+                    acc = __dp4a(d0, d0, acc);
+                    acc = __dp4a(d1, d1, acc);
+                    acc = __dp4a(d2, d2, acc);
+                    acc = __dp4a(d3, d3, acc);
+                } else {
+                    df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(b.x), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(b.y), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(b.z), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(b.w), hi, lo);
+                }
+            }
+        }
+        for (int off = G >> 1; off > 0; off >>= 1) {
+            if (DT == ANN_U8) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            } else {
+                float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                df_add(hi, lo, h2, l2);
+            }
+        }
+        if (act && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// bridge batch walk
+// ---------------------------------------------------------------------------
+struct WalkState {
+    uint64_t lo;      // every non-empty bridge with composite <= lo has been produced
+    bool first;       // nothing produced yet (lo meaningless)
+    bool exhausted;   // all non-empty bridges produced
+    uint32_t width;   // window width in key units (u8) or key-bit units (f32)
+    uint32_t kmin, kmaxall, msuf;
+};
+
+// Emit the composite (key << 32 | packed ranks) of every non-empty bridge with
+// lo < composite <= hi (lo ignored when first).  Returns how many there were;
+// only the first bcap are stored.  Two phases per chunk: (1) the prefix
+// nodes (c0[, c1]) whose lower bound fits the window and that hold bridges
+// are collected into a node list; (2) the suffix leaves of the listed nodes
+// are processed as one flat range, 32 consecutive leaves per step.
+template <int DT>
+__device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
+                         uint64_t hi, int64_t *st_nodes, int64_t *st_leaves) {
+    const int lane = lane_id();
+    const int n = ix.n, P = ix.P, PA = ix.PA;
+    const uint32_t *D = (const uint32_t *)(smem + L.tabD);
+    const uint8_t *rk = smem + L.rank;
+    const uint32_t *sk = (const uint32_t *)(smem + L.sk);
+    const uint8_t *sc = smem + L.sc;
+    uint32_t *pref = (uint32_t *)(smem + L.pref);
+    uint32_t *nodes = (uint32_t *)(smem + L.nodes);  // 4 words per node: start, count, kpre, rpre
+    uint64_t *bkey = (uint64_t *)(smem + L.bkey);
+    uint32_t *bidx = (uint32_t *)(smem + L.bidx);
+    uint32_t *cnt = (uint32_t *)(smem + L.misc);
+    const uint32_t hik = (uint32_t)(hi >> 32);
+    const uint32_t msuf = cnt[3];  // min-suffix key sum, stored by the caller
+    const int nsuf = P - PA;
+    if (lane == 0) cnt[0] = 0;
+    // candidate part-1 ranks per r0 (PA == 2), or 0/1 per r0 (PA == 1)
+    for (int r0 = lane; r0 < n; r0 += 32) {
+        uint32_t c;
+        if (PA == 1) {
+            c = KeyOps<DT>::add(sk[r0], msuf) <= hik ? 1u : 0u;
+        } else {
+            uint32_t a0 = sk[r0];
+            if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk[n]), msuf) > hik) {
+                c = 0;
+            } else {
+                int lo1 = 1, hi1 = n;  // answer in [1, n]
+                while (lo1 < hi1) {
+                    int mid = (lo1 + hi1 + 1) >> 1;
+                    if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk[n + mid - 1]), msuf) <= hik) lo1 = mid;
+                    else hi1 = mid - 1;
+                }
+                c = (uint32_t)lo1;
+            }
+        }
+        pref[r0] = c;
+    }
+    __syncwarp();
+    // exclusive prefix sum over pref[0..n): chunked warp scan
+    {
+        const int per = (n + 31) / 32;
+        uint32_t local = 0;
+        for (int i = 0; i < per; i++) {
+            int r = lane * per + i;
+            if (r < n) local += pref[r];
+        }
+        uint32_t incl = local;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        uint32_t run = incl - local;
+        __syncwarp();
+        for (int i = 0; i < per; i++) {
+            int r = lane * per + i;
+            if (r < n) {
+                uint32_t v = pref[r];
+                pref[r] = run;
+                run += v;
+            }
+        }
+        if (lane == 31) pref[n] = incl;
+        __syncwarp();
+    }
+    const uint32_t total = pref[n];
+    int64_t nodes_here = 0, leaves_here = 0;
+    uint32_t nl = 0;      // listed nodes (warp-uniform)
+    int r0p = 0;          // running r0 pointer of this lane
+    for (uint32_t base = 0; base < total; base += 32) {
+        uint32_t f = base + lane;
+        bool ok = false;
+        uint32_t node = 0, kpre = 0, rpre = 0;
+        if (f < total) {
+            while (r0p + 1 < n && pref[r0p + 1] <= f) r0p++;
+            int r0 = r0p;
+            int r1 = (int)(f - pref[r0]);
+            uint32_t c0 = sc[r0];
+            if (PA == 1) {
+                node = c0;
+                kpre = D[c0];
+                rpre = (uint32_t)r0;
+            } else {
+                uint32_t c1 = sc[n + r1];
+                node = c0 * n + c1;
+                kpre = KeyOps<DT>::add(D[c0], D[n + c1]);
+                rpre = ((uint32_t)r0 << 8) | (uint32_t)r1;
+            }
+            ok = (__ldg(ix.bmA + (node >> 5)) >> (node & 31)) & 1u;
+        }
+        nodes_here += (f < total);
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            uint32_t pos = nl + __popc(m & ((1u << lane) - 1));
+            uint32_t j0 = __ldg(ix.offA + node), j1 = __ldg(ix.offA + node + 1);
+            nodes[4 * pos + 0] = j0;
+            nodes[4 * pos + 1] = j1 - j0;
+            nodes[4 * pos + 2] = kpre;
+            nodes[4 * pos + 3] = rpre;
+        }
+        nl += __popc(m);
+        bool flush = (nl + 32 > L.ncap) || (base + 32 >= total);
+        if (flush && nl > 0) {
+            __syncwarp();
+            // prefix over listed nodes' leaf counts (reuse the count word as its start in flat space)
+            uint32_t run = 0;
+            for (uint32_t b0 = 0; b0 < nl; b0 += 32) {
+                uint32_t i = b0 + lane;
+                uint32_t c = i < nl ? nodes[4 * i + 1] : 0;
+                uint32_t incl = c;
+                for (int off = 1; off < 32; off <<= 1) {
+                    uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                    if (lane >= off) incl += v;
+                }
+                if (i < nl) nodes[4 * i + 1] = run + incl - c;  // flat start of node i
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+            __syncwarp();
+            const uint32_t lt = run;
+            uint32_t np = 0;  // running node pointer of this lane
+            for (uint32_t g = lane; g < lt; g += 32) {
+                while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
+                uint32_t j = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
+                uint32_t lf = __ldg(ix.leaf + j);
+                uint32_t ksuf, rsuf;
+                if (nsuf == 1) {
+                    ksuf = D[(P - 1) * n + lf];
+                    rsuf = rk[(P - 1) * n + lf];
+                } else {
+                    uint32_t c2 = lf / n, c3 = lf - (lf / n) * n;
+                    ksuf = KeyOps<DT>::add(D[2 * n + c2], D[3 * n + c3]);
+                    rsuf = ((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3];
+                }
+                uint32_t key = KeyOps<DT>::add(nodes[4 * np + 2], ksuf);
+                uint32_t ranks = (nodes[4 * np + 3] << (8 * nsuf)) | rsuf;
+                uint64_t comp = ((uint64_t)key << 32) | ranks;
+                if (comp <= hi && (first || comp > lo)) {
+                    uint32_t s = atomicAdd(&cnt[0], 1u);
+                    if (s < L.bcap) {
+                        bkey[s] = comp;
+                        bidx[s] = j;
+                    }
+                }
+            }
+            leaves_here += lt;
+            nl = 0;
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    for (int off = 16; off > 0; off >>= 1) nodes_here += __shfl_xor_sync(0xffffffffu, nodes_here, off);
+    if (lane == 0) {
+        *st_nodes += nodes_here;
+        *st_leaves += leaves_here;
+    }
+    __syncwarp();
+    return cnt[0];
+}
+
+// next window end (composite) from lo with width w, capped at the largest key
+__device__ __forceinline__ uint64_t window_end(uint64_t lo, bool first, uint32_t kmin, uint32_t w,
+                                               uint32_t kmaxall) {
+    uint32_t base = first ? kmin : (uint32_t)(lo >> 32);
+    uint64_t e = (uint64_t)base + (uint64_t)w;
+    if (e > kmaxall) e = kmaxall;
+    return (e << 32) | 0xffffffffull;
+}
+
+// Refill the batch: bridges after ws.lo in order.  Returns count (0 = none left).
+template <int DT>
+__device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, WalkState &ws,
+                           int64_t *stats, bool &cap_err) {
+    uint64_t *bkey = (uint64_t *)(smem + L.bkey);
+    uint32_t *bidx = (uint32_t *)(smem + L.bidx);
+    const int lane = lane_id();
+    while (!ws.exhausted) {
+        uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
+        uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, &stats[ANN_STAT_WALK_NODES],
+                              &stats[ANN_STAT_WALK_LEAVES]);
+        stats[ANN_STAT_WALKS]++;
+        if (c > L.bcap) {
+            // too many in the window: halve it (in composite space)
+            uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
+            uint64_t span = hi - base;
+            if (span == 0) { cap_err = true; return 0; }
+            // shrink the key width, or split inside one key by ranks
+            if (ws.width > 1) {
+                ws.width >>= 1;
+                continue;
+            }
+            // width 1 key unit: split the composite range directly
+            uint64_t h2 = base + span / 2;
+            while (true) {
+                c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, &stats[ANN_STAT_WALK_NODES],
+                             &stats[ANN_STAT_WALK_LEAVES]);
+                stats[ANN_STAT_WALKS]++;
+                if (c <= L.bcap) break;
+                span = h2 - base;
+                if (span == 0) { cap_err = true; return 0; }
+                h2 = base + span / 2;
+            }
+            hi = h2;
+        }
+        bool reached_end = (uint32_t)(hi >> 32) >= ws.kmaxall && (uint32_t)hi == 0xffffffffu;
+        ws.lo = hi;
+        ws.first = false;
+        if (reached_end) ws.exhausted = true;
+        if (c == 0) {
+            if (ws.width < 0x40000000u) ws.width <<= 1;
+            continue;
+        }
+        // grow the window while batches stay small
+        if (c < L.bcap / 8 && ws.width < 0x40000000u) ws.width <<= 2;
+        else if (c < L.bcap / 4 && ws.width < 0x40000000u) ws.width <<= 1;
+        // sort the batch
+        uint32_t Lp = 1;
+        while (Lp < c) Lp <<= 1;
+        for (uint32_t i = c + lane; i < Lp; i += 32) {
+            bkey[i] = ~0ull;
+            bidx[i] = 0;
+        }
+        __syncwarp();
+        warp_sort_pairs(bkey, bidx, (int)Lp);
+        return c;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// one query, one warp
+// ---------------------------------------------------------------------------
+template <int DT>
+__device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
+    const DevIndex &ix = A.ix;
+    const WarpLayout &L = A.L;
+    const int lane = lane_id();
+    const int n = ix.n, P = ix.P, PA = ix.PA, dp = ix.d / ix.P;
+    const int k = A.k ? A.k[qi] : A.k_all;
+    const int T = A.T ? A.T[qi] : A.T_all;
+    int32_t *oid = A.out_ids + qi * A.kmax;
+    int64_t stats[ANN_NSTATS];
+    for (int i = 0; i < ANN_NSTATS; i++) stats[i] = 0;
+    if (k < 0 || k > A.kmax || T < 0 || T > A.capT) {
+        for (int j = lane; j < A.kmax; j += 32) {
+            oid[j] = -1;
+            if (A.out_keys) ((uint32_t *)A.out_keys)[qi * A.kmax + j] = DT == ANN_U8 ? 0xffffffffu : 0x7f800000u;
+        }
+        if (A.out_status && lane == 0) A.out_status[qi] = ANN_ERR_ARG;
+        return;
+    }
+    uint8_t *qb = smem + L.q;
+    uint32_t *D = (uint32_t *)(smem + L.tabD);
+    uint8_t *rk = smem + L.rank;
+    uint32_t *sk = (uint32_t *)(smem + L.sk);
+    uint8_t *sc = smem + L.sc;
+    uint64_t *heap = (uint64_t *)(smem + L.heap);
+    uint32_t *H = (uint32_t *)(smem + L.hash);
+    uint64_t *rbuf = (uint64_t *)(smem + L.rbuf);
+    uint64_t *bkey = (uint64_t *)(smem + L.bkey);
+    uint32_t *bidx = (uint32_t *)(smem + L.bidx);
+    uint32_t *cand = (uint32_t *)(smem + L.cand);
+    uint32_t *ckey = (uint32_t *)(smem + L.ckey);
+    uint32_t *misc = (uint32_t *)(smem + L.misc);
+
+    // load the query
+    const int vb = ix.d * (DT == ANN_U8 ? 1 : 4);
+    {
+        const uint4 *src = (const uint4 *)((const uint8_t *)A.queries + qi * (int64_t)vb);
+        uint4 *dst = (uint4 *)qb;
+        for (int c = lane; c < (vb >> 4); c += 32) dst[c] = __ldg(src + c);
+    }
+    // clear the visited set
+    for (uint32_t i = lane; i < (1u << L.hash_log); i += 32) H[i] = 0;
+    __syncwarp();
+
+    // 1. part tables
+    for (int idx = lane; idx < P * n; idx += 32) {
+        int p = idx / n, c = idx % n;
+        D[idx] = part_key_lane<DT>(qb, ix.C, p, c, n, dp);
+    }
+    __syncwarp();
+    // 2. per-part sort by (key, center id); ranks for every part, sorted keys/ids for prefix parts
+    uint32_t msuf = 0;
+    uint32_t kmin = 0, kmaxall = 0;
+    {
+        uint64_t *tmp = heap;  // heap is empty until the main loop
+        int Lp = 1;
+        while (Lp < n) Lp <<= 1;
+        uint32_t first_keys[kMaxP], last_keys[kMaxP];
+        for (int p = 0; p < P; p++) {
+            for (int i = lane; i < Lp; i += 32)
+                tmp[i] = i < n ? (((uint64_t)D[p * n + i]) << 32) | (uint32_t)i : ~0ull;
+            __syncwarp();
+            warp_sort_pairs(tmp, nullptr, Lp);
+            for (int r = lane; r < n; r += 32) {
+                uint32_t c = (uint32_t)tmp[r];
+                rk[p * n + c] = (uint8_t)r;
+                if (p < PA) {
+                    sk[p * n + r] = (uint32_t)(tmp[r] >> 32);
+                    sc[p * n + r] = (uint8_t)c;
+                }
+            }
+            first_keys[p] = (uint32_t)(tmp[0] >> 32);
+            last_keys[p] = (uint32_t)(tmp[n - 1] >> 32);
+            __syncwarp();
+        }
+        // smallest / largest bridge keys and the min-suffix sum, grouped (D0+D1)+(D2+...)
+        auto group_sum = [&](const uint32_t *v) -> uint32_t {
+            uint32_t a = KeyOps<DT>::add(v[0], v[1]);
+            if (P == 2) return a;
+            uint32_t b = v[2];
+            for (int p = 3; p < P; p++) b = KeyOps<DT>::add(b, v[p]);
+            return KeyOps<DT>::add(a, b);
+        };
+        kmin = group_sum(first_keys);
+        kmaxall = group_sum(last_keys);
+        if (PA == 1) {
+            msuf = first_keys[1];
+        } else {
+            msuf = first_keys[2];
+            for (int p = 3; p < P; p++) msuf = KeyOps<DT>::add(msuf, first_keys[p]);
+        }
+    }
+    if (lane == 0) misc[3] = msuf;
+    __syncwarp();
+
+    // 3. Algorithm 1
+    WalkState ws;
+    ws.lo = 0;
+    ws.first = true;
+    ws.exhausted = ix.M == 0;
+    ws.kmin = kmin;
+    ws.kmaxall = kmaxall;
+    ws.msuf = msuf;
+    if (DT == ANN_U8) {
+        uint32_t w = kmin >> 6;
+        ws.width = w < 1 ? 1 : w;
+    } else {
+        ws.width = 1u << 16;  // about 0.8% relative in float32 bit space
+    }
+    uint32_t bcur = 0, bcnt = 0;
+    uint32_t hsz = 0;       // heap size (lane 0's view is authoritative; broadcast below)
+    uint32_t rlen = 0;
+    int t = 0;
+    bool cap_err = false;
+    int64_t maxq = 0;
+    const int b = ix.b, R = ix.R;
+
+    while (t < T) {
+        if (bcur >= bcnt && !ws.exhausted) {
+            bcnt = refill<DT>(ix, smem, L, ws, stats, cap_err);
+            bcur = 0;
+            if (cap_err) break;
+        }
+        bool hb = bcur < bcnt;
+        bool hr = hsz > 0;
+        if (!hb && !hr) break;
+        uint64_t top = hr ? heap[0] : ~0ull;
+        uint64_t bc = hb ? bkey[bcur] : ~0ull;
+        bool take_ref = hr && (!hb || (uint32_t)(top >> 32) <= (uint32_t)(bc >> 32));
+        int32_t x = -1;
+        int alen;
+        if (take_ref) {
+            uint32_t p = (uint32_t)top;
+            __syncwarp();
+            if (lane == 0) heap_pop(heap, hsz);
+            __syncwarp();
+            hsz = __shfl_sync(0xffffffffu, hsz, 0);
+            alen = R;
+            if (lane < R) x = __ldg(ix.G + (int64_t)p * R + lane);
+            stats[ANN_STAT_REF_POPS]++;
+        } else {
+            uint32_t j = bidx[bcur];
+            bcur++;
+            alen = b;
+            if (lane < b) x = __ldg(ix.brefs + (int64_t)j * b + lane);
+            stats[ANN_STAT_BRIDGE_POPS]++;
+        }
+        bool isnew = lane < alen && x >= 0 && x < ix.N && !hash_has(H, L.hash_log, (uint32_t)x);
+        unsigned mask = __ballot_sync(0xffffffffu, isnew);
+        int room = T - t;
+        while (__popc(mask) > room) mask &= ~(1u << (31 - __clz(mask)));  // keep the first `room` in list order
+        int m = __popc(mask);
+        if (m == 0) continue;
+        if ((mask >> lane) & 1u) {
+            int pos = __popc(mask & ((1u << lane) - 1));
+            cand[pos] = (uint32_t)x;
+            hash_add(H, L.hash_log, (uint32_t)x);
+        }
+        __syncwarp();
+        cand_distances<DT>(ix, qb, cand, m, ckey);
+        if (lane == 0) {
+            for (int j = 0; j < m; j++) {
+                uint64_t e = ((uint64_t)ckey[j] << 32) | cand[j];
+                heap_push(heap, hsz, e);
+            }
+        }
+        __syncwarp();
+        hsz = __shfl_sync(0xffffffffu, hsz, 0);
+        if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
+        // result set: k smallest by (key, id), kept sorted in rbuf
+        for (int j = 0; j < m; j++) {
+            uint64_t e = ((uint64_t)ckey[j] << 32) | cand[j];
+            if (k == 0) break;
+            if ((int)rlen == k && e >= rbuf[k - 1]) continue;
+            // position = number of entries smaller than e
+            int cntless = 0;
+            for (int i = lane; i < (int)rlen; i += 32) cntless += rbuf[i] < e;
+            for (int off = 16; off > 0; off >>= 1) cntless += __shfl_xor_sync(0xffffffffu, cntless, off);
+            int newlen = (int)rlen < k ? (int)rlen + 1 : k;
+            // shift [cntless, newlen-1) up by one, top-down in chunks of 32
+            for (int top_i = newlen - 1; top_i > cntless; top_i -= 32) {
+                int i = top_i - lane;
+                uint64_t v = 0;
+                bool mv = i > cntless;
+                if (mv) v = rbuf[i - 1];
+                __syncwarp();
+                if (mv) rbuf[i] = v;
+                __syncwarp();
+            }
+            if (lane == 0) rbuf[cntless] = e;
+            rlen = (uint32_t)newlen;
+            __syncwarp();
+        }
+        t += m;
+    }
+    stats[ANN_STAT_DISCOVERED] = t;
+    stats[ANN_STAT_MAX_Q] = maxq;
+    __syncwarp();
+    // outputs
+    for (int j = lane; j < A.kmax; j += 32) {
+        bool have = j < (int)rlen && j < k;
+        oid[j] = have ? (int32_t)(uint32_t)rbuf[j] : -1;
+        if (A.out_keys) {
+            uint32_t kv = have ? (uint32_t)(rbuf[j] >> 32) : (DT == ANN_U8 ? 0xffffffffu : 0x7f800000u);
+            ((uint32_t *)A.out_keys)[qi * A.kmax + j] = kv;
+        }
+    }
+    if (lane == 0) {
+        if (A.out_status) A.out_status[qi] = cap_err ? ANN_ERR_CAPACITY : ANN_OK;
+        if (A.out_stats)
+            for (int i = 0; i < ANN_NSTATS; i++) A.out_stats[qi * ANN_NSTATS + i] = stats[i];
+    }
+    __syncwarp();
+}
+
+template <int DT>
+__global__ void __launch_bounds__(512) search_kernel(SearchArgs A) {
+    extern __shared__ __align__(16) uint8_t smem_all[];
+    const int warp = threadIdx.x >> 5;
+    uint8_t *smem = smem_all + (size_t)warp * A.L.total;
+    const int64_t count = A.list_count ? (int64_t)*A.list_count : (A.list ? A.list_len : A.nq);
+    if (A.ticket) {
+        // persistent: pull queries from the device work queue
+        for (;;) {
+            int32_t w = 0;
+            if (lane_id() == 0) w = atomicAdd(A.ticket, 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (w >= count) break;
+            int64_t qi = A.list ? A.list[w] : w;
+            search_one<DT>(A, smem, qi);
+        }
+    } else {
+        const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+        for (int64_t w = gw; w < count; w += nw) {
+            int64_t qi = A.list ? A.list[w] : w;
+            search_one<DT>(A, smem, qi);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int g_num_sms = 0;
+static size_t g_smem_optin = 0;
+
+static int device_props() {
+    if (g_num_sms) return ANN_OK;
+    int dev;
+    ANN_CUDA(cudaGetDevice(&dev));
+    cudaDeviceProp prop;
+    ANN_CUDA(cudaGetDeviceProperties(&prop, dev));
+    g_num_sms = prop.multiProcessorCount;
+    g_smem_optin = prop.sharedMemPerBlockOptin;
+    return ANN_OK;
+}
+
+// Launch configuration for a budget bucket: warps per CTA and batch capacity.
+struct Tune {
+    int warps;
+    int bcap;
+};
+
+// Warps per CTA: the count that keeps the most warps resident per SM given
+// the per-warp shared-memory slice (ties go to more warps per CTA).
+static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
+    Tune t;
+    t.bcap = 256;
+    WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap);
+    const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
+    size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
+    int best_w = 1, best_res = 0;
+    for (int w = 1; w <= 8; w++) {
+        size_t cta = (size_t)w * L.total;
+        if (cta > budget) break;
+        int ctas = (int)(per_sm / (cta + per_cta_reserved));
+        if (ctas > 32 / w) ctas = 32 / w;
+        int res = ctas * w;
+        if (res >= best_res) {
+            best_res = res;
+            best_w = w;
+        }
+    }
+    t.warps = best_w;
+    return t;
+}
+
+static int launch_search(const SearchArgs &base, int capT, cudaStream_t stream, bool persistent,
+                         const int32_t *list, const int32_t *list_count, int64_t list_len,
+                         int32_t *ticket) {
+    SearchArgs A = base;
+    A.capT = capT;
+    Tune tn = choose_tune(A.ix, capT, A.kmax);
+    A.bcap = tn.bcap;
+    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap);
+    A.list = list;
+    A.list_count = list_count;
+    A.list_len = list_len;
+    A.ticket = ticket;
+    size_t smem = (size_t)A.L.total * tn.warps;
+    if (smem > g_smem_optin) return fail(ANN_ERR_CAPACITY, "per-query state exceeds shared memory");
+    int blocks_per_sm = 0;
+    if (A.ix.dtype == ANN_U8) {
+        ANN_CUDA(cudaFuncSetAttribute(search_kernel<ANN_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        ANN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, search_kernel<ANN_U8>,
+                                                               tn.warps * 32, smem));
+    } else {
+        ANN_CUDA(cudaFuncSetAttribute(search_kernel<ANN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        ANN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, search_kernel<ANN_F32>,
+                                                               tn.warps * 32, smem));
+    }
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    int64_t want = list_count ? (int64_t)g_num_sms * blocks_per_sm
+                              : (list_len + tn.warps - 1) / tn.warps;
+    int64_t cap = (int64_t)g_num_sms * blocks_per_sm;
+    if (!persistent && !list_count) {
+        // plain: one warp per query, at most a full wave resident, grid-stride beyond
+        if (want > cap * 4) want = cap * 4;
+    } else {
+        want = cap;
+    }
+    if (want < 1) want = 1;
+    dim3 grid((unsigned)want), block(tn.warps * 32);
+    if (A.ix.dtype == ANN_U8) search_kernel<ANN_U8><<<grid, block, smem, stream>>>(A);
+    else search_kernel<ANN_F32><<<grid, block, smem, stream>>>(A);
+    ANN_CUDA(cudaGetLastError());
+    return ANN_OK;
+}
+
+__global__ void max_kernel(const int32_t *v, int64_t n, int32_t *out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) atomicMax(out, v[i]);
+}
+
+// ---- persistent mode: bucket queries by budget on the device ----
+static const int kBuckets = 7;  // capT = 128 << i  (128 .. 8192)
+
+__global__ void bucket_kernel(int64_t nq, const int32_t *T, int32_t T_all, int32_t *counts,
+                              int32_t *lists, int32_t *tickets) {
+    // counts[kBuckets], lists[kBuckets * nq]
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nq) return;
+    int t = T ? T[i] : T_all;
+    int bkt = 0;
+    while (bkt < kBuckets - 1 && t > (128 << bkt)) bkt++;
+    int pos = atomicAdd(&counts[bkt], 1);
+    lists[(int64_t)bkt * nq + pos] = (int32_t)i;
+}
+
+struct Plan {
+    cudaGraphExec_t exec = nullptr;
+    int32_t *scratch = nullptr;  // counts[kBuckets] + tickets[kBuckets] + lists[kBuckets*nq]
+};
+
+struct PlanKey {
+    const void *queries;
+    int64_t nq;
+    const int32_t *k, *T;
+    int32_t k_all, T_all, kmax;
+    int32_t *out_ids;
+    void *out_keys;
+    int32_t *out_status;
+    int64_t *out_stats;
+    cudaStream_t stream;
+    bool operator<(const PlanKey &o) const {
+        return std::tie(queries, nq, k, T, k_all, T_all, kmax, out_ids, out_keys, out_status, out_stats, stream) <
+               std::tie(o.queries, o.nq, o.k, o.T, o.k_all, o.T_all, o.kmax, o.out_ids, o.out_keys, o.out_status,
+                        o.out_stats, o.stream);
+    }
+};
+
+struct PlanCache {
+    std::mutex mu;
+    std::map<PlanKey, Plan> plans;
+};
+
+void free_plans(ann_index *ix) {
+    if (!ix->plans) return;
+    PlanCache *pc = (PlanCache *)ix->plans;
+    for (auto &kv : pc->plans) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.scratch) cudaFree(kv.second.scratch);
+    }
+    delete pc;
+    ix->plans = nullptr;
+}
+
+static int record_persistent(const SearchArgs &A, int64_t nq, const int32_t *T, int32_t T_all,
+                             int32_t *scratch, cudaStream_t s) {
+    int32_t *counts = scratch, *tickets = scratch + kBuckets, *lists = scratch + 2 * kBuckets;
+    ANN_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2 * kBuckets, s));
+    if (nq > 0) {
+        bucket_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, T, T_all, counts, lists, tickets);
+        ANN_CUDA(cudaGetLastError());
+    }
+    int maxb = kBuckets - 1;
+    if (!T) {
+        maxb = 0;
+        while (maxb < kBuckets - 1 && T_all > (128 << maxb)) maxb++;
+    }
+    for (int bkt = (T ? 0 : maxb); bkt <= maxb; bkt++) {
+        int capT = 128 << bkt;
+        if (capT > kMaxT) capT = kMaxT;
+        int r = launch_search(A, capT, s, true, lists + (int64_t)bkt * nq, counts + bkt, nq, tickets + bkt);
+        if (r != ANN_OK) return r;
+    }
+    return ANN_OK;
+}
+
+}  // namespace ann
+
+using namespace ann;
+
+extern "C" int ann_search_batch(const ann_index *index, const void *queries, int64_t nq, const int32_t *k,
+                                const int32_t *T, int32_t k_all, int32_t T_all, int32_t kmax, int32_t mode,
+                                int32_t *out_ids, void *out_keys, int32_t *out_status, int64_t *out_stats,
+                                void *stream) {
+    ANN_ARG(index != nullptr, "index is NULL");
+    ANN_ARG(nq >= 0 && nq < (1ll << 31), "nq out of range");
+    ANN_ARG(kmax >= 1 && kmax <= kMaxK, "kmax must be in [1, 128]");
+    ANN_ARG(mode == ANN_MODE_PLAIN || mode == ANN_MODE_PERSISTENT, "mode must be 0 (plain) or 1 (persistent)");
+    ANN_ARG(nq == 0 || (queries && out_ids), "queries and out_ids are required");
+    ANN_ARG(((uintptr_t)queries & 15) == 0, "queries must be 16-byte aligned");
+    if (!k) ANN_ARG(k_all >= 0 && k_all <= kmax, "k_all must be in [0, kmax]");
+    if (!T) ANN_ARG(T_all >= 0 && T_all <= kMaxT, "T_all must be in [0, 8192]");
+    int r = device_props();
+    if (r != ANN_OK) return r;
+    if (nq == 0) return ANN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    SearchArgs A{};
+    A.ix = index->dev;
+    A.queries = queries;
+    A.nq = nq;
+    A.k = k;
+    A.T = T;
+    A.k_all = k_all;
+    A.T_all = T_all;
+    A.kmax = kmax;
+    A.out_ids = out_ids;
+    A.out_keys = out_keys;
+    A.out_status = out_status;
+    A.out_stats = out_stats;
+    if (mode == ANN_MODE_PLAIN) {
+        // one launch sized for the largest budget in the batch
+        int capT = T_all;
+        if (T) {
+            int32_t *dmax = nullptr, hmax = 0;
+            ANN_CUDA(cudaMallocAsync((void **)&dmax, sizeof(int32_t), s));
+            ANN_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+            max_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(T, nq, dmax);
+            ANN_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            ANN_CUDA(cudaFreeAsync(dmax, s));
+            ANN_CUDA(cudaStreamSynchronize(s));
+            capT = hmax;
+        }
+        if (capT > kMaxT) capT = kMaxT;
+        if (capT < 32) capT = 32;
+        return launch_search(A, capT, s, false, nullptr, nullptr, nq, nullptr);
+    }
+    // persistent: bucket by budget, one persistent kernel per bucket, replayed as a CUDA graph
+    ann_index *ixm = const_cast<ann_index *>(index);
+    if (!ixm->plans) ixm->plans = new PlanCache();
+    PlanCache *pc = (PlanCache *)ixm->plans;
+    PlanKey key{queries, nq, k, T, k_all, T_all, kmax, out_ids, out_keys, out_status, out_stats, s};
+    std::lock_guard<std::mutex> g(pc->mu);
+    auto it = pc->plans.find(key);
+    if (it == pc->plans.end()) {
+        Plan p;
+        ANN_CUDA(cudaMalloc(&p.scratch, sizeof(int32_t) * (2 * kBuckets + (size_t)kBuckets * nq)));
+        cudaStream_t cap;
+        ANN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        ANN_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        int rr = record_persistent(A, nq, T, T_all, p.scratch, cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        cudaStreamDestroy(cap);
+        if (rr != ANN_OK) {
+            cudaFree(p.scratch);
+            return rr;
+        }
+        if (ce != cudaSuccess) {
+            cudaFree(p.scratch);
+            return cuda_fail(ce, "cudaStreamEndCapture");
+        }
+        ce = cudaGraphInstantiate(&p.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            cudaFree(p.scratch);
+            return cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        it = pc->plans.emplace(key, p).first;
+    }
+    ANN_CUDA(cudaGraphLaunch(it->second.exec, s));
+    return ANN_OK;
+}

@@ -1,0 +1,49 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/ann.h declares (no GPU needed, no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1312_3062_gb300 import _build
+    return _build.build()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ann.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ann_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("ann_index_load", "ann_build_knn_graph", "ann_search_batch", "ann_serve_submit",
+                 "ann_serve_poll"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header(libpath):
+    from paper_1312_3062_gb300 import ann
+    assert sorted(ann.EXPORTED) == declared_symbols()
+
+
+def test_argument_errors_need_no_gpu(libpath):
+    # argument validation happens before any CUDA call
+    from paper_1312_3062_gb300 import ann
+    rc = ann.lib.ann_exact_knn(None, 0, None, 0, 0, 128, 10, 0, None, None, None)
+    assert rc == ann.ANN_ERR_ARG
+    assert b"N or nq" in ann.lib.ann_last_error()
+    rc = ann.lib.ann_search_batch(None, None, 1, None, None, 1, 1, 1, 0, None, None, None, None, None)
+    assert rc == ann.ANN_ERR_ARG and b"index is NULL" in ann.lib.ann_last_error()

@@ -56,10 +56,16 @@ def part_tables(q, centers):
 def bridge_key_py(parts_keys, dtype):
     if np.dtype(dtype) == np.uint8:
         return float(sum(int(v) for v in parts_keys))
-    s = np.float32(parts_keys[0])
-    for v in parts_keys[1:]:
-        s = np.float32(s + np.float32(v))
-    return float(s)
+    v = [np.float32(x) for x in parts_keys]
+    if len(v) == 1:
+        return float(v[0])
+    a = np.float32(v[0] + v[1])
+    if len(v) == 2:
+        return float(a)
+    b = v[2]
+    for x in v[3:]:
+        b = np.float32(b + x)
+    return float(np.float32(a + b))
 
 
 def all_bridges_sorted(D, dtype):
@@ -220,7 +226,8 @@ def test_round_centers_half_even_and_clip(oracle_lib):
 # --------------------------------------------------------------------------
 
 @pytest.mark.parametrize("P,n,dtype", [(2, 64, np.uint8), (3, 16, np.uint8), (4, 8, np.uint8),
-                                       (2, 24, np.float32), (3, 10, np.float32)])
+                                       (2, 24, np.float32), (3, 10, np.float32),
+                                       (4, 6, np.float32)])
 def test_multiseq_equals_full_sort(oracle_lib, P, n, dtype):
     rng = np.random.default_rng(10 + P * n)
     if dtype == np.uint8:
