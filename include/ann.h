@@ -71,6 +71,24 @@ int ann_exact_knn(const void *refs, int64_t N, const void *queries, int64_t nq, 
                   int32_t d, int32_t k, int32_t exclude_self, int32_t *out_ids, void *out_keys,
                   void *stream);
 
+/* Same computation and arguments as ann_exact_knn, but the call allocates
+ * nothing: the uint8 row norms it needs live in a fixed array inside the
+ * library (4 MiB, 1048576 rows), which every GPU that loads the library keeps
+ * until the process exits.  The paper has no counterpart; it exists for
+ * callers that cannot allocate device memory themselves (a host program
+ * whose device memory belongs to another allocator, or a latency-critical
+ * loop that cannot take an allocation's synchronisation and latency).
+ * Limits: for ANN_U8, N plus nq (nq counts only when queries != refs) must
+ * not exceed 1048576, otherwise ANN_ERR_CAPACITY; ANN_F32 needs no scratch.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call
+ * shares the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race: serialise them.  Nothing in the array needs to
+ * start at zero -- each call writes every norm it reads.  Asynchronous. */
+int ann_exact_knn_static(const void *refs, int64_t N, const void *queries, int64_t nq, int dtype,
+                         int32_t d, int32_t k, int32_t exclude_self, int32_t *out_ids,
+                         void *out_keys, void *stream);
+
 /* Exact R-NN neighbourhood graph of data (Sec. 3.1, Sec. 4.1): same as
  * ann_exact_knn(data, N, data, N, dtype, d, R, 1, ...). */
 int ann_build_knn_graph(const void *data, int dtype, int64_t N, int32_t d, int32_t R,

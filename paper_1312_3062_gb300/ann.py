@@ -53,6 +53,7 @@ def _sig(name, argtypes, restype=ctypes.c_int):
 
 _sig("ann_last_error", [], ctypes.c_char_p)
 _sig("ann_exact_knn", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_])
+_sig("ann_exact_knn_static", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_])
 _sig("ann_build_knn_graph", [P_, ctypes.c_int, i64, i32, i32, P_, P_, P_])
 _sig("ann_train_centers", [P_, ctypes.c_int, i64, i32, i32, i32, i32, P_, P_, P_, P_])
 _sig("ann_index_create", [ctypes.POINTER(ann_index_desc), ctypes.POINTER(P_)])
@@ -68,7 +69,7 @@ _sig("ann_serve_submit", [P_, P_, i32, P_, P_, ctypes.POINTER(u64)])
 _sig("ann_serve_poll", [P_, u64, P_, P_, P_])
 _sig("ann_serve_latency", [P_, u64], f64)
 
-EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_build_knn_graph", "ann_train_centers", "ann_index_create",
+EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_train_centers", "ann_index_create",
             "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges",
             "ann_search_batch", "ann_server_create", "ann_server_destroy", "ann_serve_submit", "ann_serve_poll",
             "ann_serve_latency")

@@ -12,6 +12,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "ann_device.cuh"
 #include "ann_internal.cuh"
@@ -243,4 +244,85 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
 extern "C" int ann_build_knn_graph(const void *data, int dtype, int64_t N, int32_t d, int32_t R, int32_t *out_ids,
                                    void *out_keys, void *stream) {
     return ann_exact_knn(data, N, data, N, dtype, d, R, 1, out_ids, out_keys, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Exact k-NN without any allocation: the row norms live in a file-scope
+// device array instead of memory obtained from cudaMallocAsync.  Meant for
+// callers that may not allocate device memory themselves, such as a host
+// program whose device memory is owned entirely by another allocator (a
+// framework's caching allocator or a fixed pool that must remain the only
+// owner), or a latency-critical loop that cannot afford an allocation's
+// device-wide synchronisation and unbounded latency.
+// ---------------------------------------------------------------------------
+namespace ann {
+
+static const int64_t kStaticNormRows = 1 << 20;  // 4 MiB of uint32 norms
+static __device__ __align__(256) uint32_t g_static_norms[kStaticNormRows];
+
+static std::mutex g_static_mu;
+static uint32_t *g_static_ptr[64];  // device address of g_static_norms, per device ordinal
+
+// Device address of the array on the current device; looked up once per device.
+static int static_norms_ptr(uint32_t **out) {
+    int dev = 0;
+    ANN_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(ANN_ERR_ARG, "device ordinal out of range for the static scratch table");
+    std::lock_guard<std::mutex> g(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_norms);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static norms)");
+        g_static_ptr[dev] = (uint32_t *)p;
+    }
+    *out = g_static_ptr[dev];
+    return ANN_OK;
+}
+
+}  // namespace ann
+
+extern "C" int ann_exact_knn_static(const void *refs, int64_t N, const void *queries, int64_t nq, int dtype,
+                                    int32_t d, int32_t k, int32_t exclude_self, int32_t *out_ids, void *out_keys,
+                                    void *stream) {
+    ANN_ARG(dtype == ANN_U8 || dtype == ANN_F32, "dtype must be ANN_U8 or ANN_F32");
+    ANN_ARG(N >= 1 && N < (1ll << 31) && nq >= 0 && nq < (1ll << 31), "N or nq out of range");
+    ANN_ARG(k >= 1 && k <= 32, "k must be in [1, 32]");
+    ANN_ARG(dtype == ANN_U8 ? (d >= 16 && d % 16 == 0) : (d >= 4 && d % 4 == 0),
+            "d must be a multiple of 16 (u8) or 4 (f32)");
+    ANN_ARG(refs && (nq == 0 || (queries && out_ids)), "refs, queries and out_ids are required");
+    ANN_ARG(!exclude_self || (queries == refs && nq == N), "exclude_self needs queries == refs");
+    const bool shared = queries == refs;
+    const int64_t rows = dtype == ANN_U8 ? N + (shared ? 0 : nq) : 0;
+    if (rows > kStaticNormRows)
+        return fail(ANN_ERR_CAPACITY, "ann_exact_knn_static: N (+ nq when queries differ from refs) exceeds the "
+                                      "static scratch of 1048576 rows; use ann_exact_knn");
+    if (nq == 0) return ANN_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *rn = nullptr, *qn = nullptr;
+    if (dtype == ANN_U8) {
+        uint32_t *base = nullptr;
+        int r = static_norms_ptr(&base);
+        if (r != ANN_OK) return r;
+        // every norm used below is written here first: nothing must start at zero
+        rn = base;
+        qn = shared ? rn : base + N;
+        norms_u8_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((const uint8_t *)refs, N, d, rn);
+        if (!shared)
+            norms_u8_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const uint8_t *)queries, nq, d, qn);
+    }
+    const int KW = dtype == ANN_U8 ? d / 4 : 64;
+    const int SW = KW + 4;
+    size_t smem = 4 * ((size_t)(KB_M + KB_N) * SW + (size_t)KB_M * (KB_N + 1) + KB_M + KB_N);
+    unsigned grid = (unsigned)((nq + KB_M - 1) / KB_M);
+    if (dtype == ANN_U8) {
+        ANN_CUDA(cudaFuncSetAttribute(knn_kernel<ANN_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        knn_kernel<ANN_U8><<<grid, KB_THREADS, smem, s>>>(refs, N, queries, nq, d, k, exclude_self, rn, qn, out_ids,
+                                                          (uint32_t *)out_keys);
+    } else {
+        ANN_CUDA(cudaFuncSetAttribute(knn_kernel<ANN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        knn_kernel<ANN_F32><<<grid, KB_THREADS, smem, s>>>(refs, N, queries, nq, d, k, exclude_self, rn, qn, out_ids,
+                                                           (uint32_t *)out_keys);
+    }
+    ANN_CUDA(cudaGetLastError());
+    return ANN_OK;
 }
