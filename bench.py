@@ -401,6 +401,7 @@ def main():
     torch.cuda.synchronize()
     st = stats.cpu().numpy()
     alg_bytes = algorithmic_bytes(st, W)
+    search_stats = {name: float(st[:, i].mean()) for i, name in enumerate(ann.STAT_NAMES[:7])}
     # search-kernel time alone, measured on its stream (plain launch = one search kernel)
     k_ms = statistics.mean(t_plain)
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
@@ -475,6 +476,7 @@ def main():
                          "kernel": "search_kernel<u8> (plain launch)",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+            "search_stats_mean_per_query": search_stats,
             "cpu_baseline": cpu_baseline,
             "clocks": clocks,
             "gpu_launches": args.steps * 2,

@@ -37,20 +37,20 @@ namespace ann {
 // shared-memory layout of one warp
 // ---------------------------------------------------------------------------
 struct WarpLayout {
-    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, misc, total;
+    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, misc, total;
     uint32_t heap_cap, hash_log, bcap, ncap;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
-                                                  int kmax, int bcap) {
+                                                  int kmax, int bcap, int b) {
     WarpLayout L;
     uint32_t o = 0;
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
     L.tabD = o;   o = align_up(o + 4u * P * n, 16);
     L.rank = o;   o = align_up(o + (uint32_t)P * n, 16);
-    L.sk = o;     o = align_up(o + 4u * PA * n, 16);
+    L.sk = 0;     // sorted keys of the prefix parts are read as D[sc[r]]
     L.sc = o;     o = align_up(o + (uint32_t)PA * n, 16);
     uint32_t lpn = 1;
     while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
@@ -65,11 +65,20 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.bcap = (uint32_t)bcap;
     L.bkey = o;   o = align_up(o + 8u * bcap, 16);
     L.bidx = o;   o = align_up(o + 4u * bcap, 16);
-    L.pref = o;   o = align_up(o + 4u * (n + 1), 16);
-    L.ncap = 128;
-    L.nodes = o;  o = align_up(o + 16u * L.ncap, 16);
-    L.cand = o;   o = align_up(o + 4u * 32, 16);
-    L.ckey = o;   o = align_up(o + 4u * 32, 16);
+    // scratch shared by the walk (prefix sums + node list) and the main loop
+    // (candidate ids + keys); the two never overlap in time
+    const uint32_t wb = 32u * (uint32_t)b;  // bridge-window entries
+    L.ncap = 64;
+    uint32_t walk_bytes = align_up(4u * (n + 1), 16) + 16u * L.ncap;
+    uint32_t cand_n = wb > 32u ? wb : 32u;
+    uint32_t main_bytes = align_up(4u * cand_n, 16) * 2;
+    L.pref = o;
+    L.nodes = o + align_up(4u * (n + 1), 16);
+    L.cand = o;
+    L.ckey = o + align_up(4u * cand_n, 16);
+    o = align_up(o + (walk_bytes > main_bytes ? walk_bytes : main_bytes), 16);
+    L.wref = o;   o = align_up(o + 4u * wb, 16);
+    L.wkey = o;   o = align_up(o + 4u * wb, 16);
     L.misc = o;   o = align_up(o + 16u * 4, 16);
     L.total = o;
     return L;
@@ -123,38 +132,73 @@ __device__ __forceinline__ void hash_add(uint32_t *H, uint32_t log, uint32_t x) 
 }
 
 // ---------------------------------------------------------------------------
-// main-queue heap of reference entries (key << 32 | id), run by lane 0
+// main queue of reference entries (key << 32 | id): a 32-ary min-heap in
+// shared memory.  Children of node i are 32i+1 .. 32i+32, so a pop reads one
+// contiguous row of children per level and the warp finds their minimum with
+// shuffles; a push appends and sifts up (rarely more than one level).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void heap_push(uint64_t *h, uint32_t &sz, uint64_t v) {
-    uint32_t i = sz++;
-    while (i > 0) {
-        uint32_t p = (i - 1) >> 1;
-        uint64_t pv = h[p];
-        if (pv <= v) break;
-        h[i] = pv;
-        i = p;
+__device__ __forceinline__ void warp_argmin(uint64_t &v, uint32_t &i) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        uint64_t ov = __shfl_xor_sync(0xffffffffu, v, off);
+        uint32_t oi = __shfl_xor_sync(0xffffffffu, i, off);
+        if (ov < v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
     }
-    h[i] = v;
 }
-__device__ __forceinline__ uint64_t heap_pop(uint64_t *h, uint32_t &sz) {
-    uint64_t top = h[0];
-    uint64_t v = h[--sz];
-    uint32_t i = 0;
-    for (;;) {
-        uint32_t l = 2 * i + 1;
-        if (l >= sz) break;
-        uint32_t r = l + 1;
-        uint32_t c = (r < sz && h[r] < h[l]) ? r : l;
-        if (h[c] >= v) break;
-        h[i] = h[c];
-        i = c;
+
+// append m entries (lane j holds entry j, j < m) and restore the heap order
+__device__ __forceinline__ void heap_push_batch(uint64_t *h, uint32_t &sz, uint64_t e, int m) {
+    const int lane = lane_id();
+    if (lane < m) h[sz + lane] = e;
+    __syncwarp();
+    if (lane == 0) {
+        for (int j = 0; j < m; j++) {
+            uint32_t i = sz + j;
+            uint64_t v = h[i];
+            while (i > 0) {
+                uint32_t p = (i - 1) >> 5;
+                uint64_t pv = h[p];
+                if (pv <= v) break;
+                h[i] = pv;
+                i = p;
+            }
+            h[i] = v;
+        }
     }
-    if (sz > 0) h[i] = v;
-    return top;
+    sz += m;
+    __syncwarp();
+}
+
+// remove the minimum (the caller has read h[0]); all lanes take part
+__device__ __forceinline__ void heap_pop(uint64_t *h, uint32_t &sz) {
+    const int lane = lane_id();
+    sz--;
+    const uint64_t v = h[sz];
+    uint32_t i = 0;
+    __syncwarp();
+    for (;;) {
+        uint32_t c0 = 32 * i + 1;
+        if (c0 >= sz) break;
+        uint32_t ci = c0 + lane;
+        uint64_t cv = ci < sz ? h[ci] : ~0ull;
+        warp_argmin(cv, ci);
+        if (cv >= v) break;
+        __syncwarp();
+        if (lane == 0) h[i] = cv;
+        i = ci;
+    }
+    __syncwarp();
+    if (lane == 0 && sz > 0) h[i] = v;
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// distance of the candidates listed in cand[0..m) to the query (keys -> ckey)
+// distances of candidate rows to the query.  cand[0..m) are row ids; keys go
+// to ckey[0..m).  A group of G lanes (G = 16-byte chunks per row, at most 32)
+// handles one row; all loads of several rows are issued before any is used.
 // ---------------------------------------------------------------------------
 template <int DT>
 __device__ void cand_distances(const DevIndex &ix, const uint8_t *qbytes, const uint32_t *cand, int m,
@@ -167,44 +211,83 @@ __device__ void cand_distances(const DevIndex &ix, const uint8_t *qbytes, const 
     const int per_round = 32 / G;
     const int lig = lane & (G - 1);
     const int grp = lane / G;
-    for (int base = 0; base < m; base += per_round) {
-        int j = base + grp;
-        bool act = j < m;
-        uint32_t acc = 0;
-        float hi = 0.f, lo = 0.f;
-        if (act) {
-            const uint4 *row = (const uint4 *)((const uint8_t *)ix.X + (int64_t)cand[j] * vb);
-            const uint4 *qv = (const uint4 *)qbytes;
-            for (int c = lig; c < nc; c += G) {
-                uint4 a = __ldg(row + c);
-                uint4 b = qv[c];
+    const int cpl = (nc + G - 1) / G;                // chunks per lane per row
+    constexpr int MAXL = 4;                          // 16-byte loads in flight per lane
+    int rounds_per_batch = MAXL / cpl;
+    if (rounds_per_batch < 1) rounds_per_batch = 1;
+    const uint4 *qv = (const uint4 *)qbytes;
+    for (int base = 0; base < m; base += per_round * rounds_per_batch) {
+        uint4 buf[MAXL];
+        // issue every load of this batch
+#pragma unroll
+        for (int u = 0; u < MAXL; u++) {
+            int r = u / cpl, c = lig + (u % cpl) * G;
+            int j = base + r * per_round + grp;
+            if (r < rounds_per_batch && u < rounds_per_batch * cpl && j < m && c < nc)
+                buf[u] = __ldg((const uint4 *)((const uint8_t *)ix.X + (int64_t)cand[j] * vb) + c);
+        }
+        // reduce row by row
+        for (int r = 0; r < rounds_per_batch; r++) {
+            int j = base + r * per_round + grp;
+            uint32_t acc = 0;
+            float hi = 0.f, lo = 0.f;
+#pragma unroll
+            for (int u = 0; u < MAXL; u++) {
+                if (u / cpl != r || u >= rounds_per_batch * cpl) continue;
+                int c = lig + (u % cpl) * G;
+                if (j >= m || c >= nc) continue;
+                uint4 a = buf[u], q = qv[c];
                 if (DT == ANN_U8) {
-                    uint32_t d0 = __vabsdiffu4(a.x, b.x), d1 = __vabsdiffu4(a.y, b.y);
-                    uint32_t d2 = __vabsdiffu4(a.z, b.z), d3 = __vabsdiffu4(a.w, b.w);
+                    uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
+                    uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
                     acc = __dp4a(d0, d0, acc);
                     acc = __dp4a(d1, d1, acc);
                     acc = __dp4a(d2, d2, acc);
                     acc = __dp4a(d3, d3, acc);
                 } else {
-                    df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(b.x), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(b.y), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(b.z), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(b.w), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
                 }
             }
-        }
-        for (int off = G >> 1; off > 0; off >>= 1) {
-            if (DT == ANN_U8) {
-                acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            } else {
-                float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
-                float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
-                df_add(hi, lo, h2, l2);
+            // rows wider than MAXL chunks per lane: stream the rest
+            if (cpl > MAXL && j < m) {
+                const uint4 *row = (const uint4 *)((const uint8_t *)ix.X + (int64_t)cand[j] * vb);
+                for (int c = lig + MAXL * G; c < nc; c += G) {
+                    uint4 a = __ldg(row + c), q = qv[c];
+                    if (DT == ANN_U8) {
+                        uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
+                        uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
+                        acc = __dp4a(d0, d0, acc);
+                        acc = __dp4a(d1, d1, acc);
+                        acc = __dp4a(d2, d2, acc);
+                        acc = __dp4a(d3, d3, acc);
+                    } else {
+                        df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
+                    }
+                }
             }
+            for (int off = G >> 1; off > 0; off >>= 1) {
+                if (DT == ANN_U8) {
+                    acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                } else {
+                    float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                    float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                    df_add(hi, lo, h2, l2);
+                }
+            }
+            if (j < m && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
         }
-        if (act && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
 // ---------------------------------------------------------------------------
@@ -231,8 +314,8 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     const int n = ix.n, P = ix.P, PA = ix.PA;
     const uint32_t *D = (const uint32_t *)(smem + L.tabD);
     const uint8_t *rk = smem + L.rank;
-    const uint32_t *sk = (const uint32_t *)(smem + L.sk);
     const uint8_t *sc = smem + L.sc;
+    auto sk = [&](int i) -> uint32_t { return D[(i / n) * n + sc[i]]; };  // sorted key of prefix rank
     uint32_t *pref = (uint32_t *)(smem + L.pref);
     uint32_t *nodes = (uint32_t *)(smem + L.nodes);  // 4 words per node: start, count, kpre, rpre
     uint64_t *bkey = (uint64_t *)(smem + L.bkey);
@@ -246,16 +329,16 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     for (int r0 = lane; r0 < n; r0 += 32) {
         uint32_t c;
         if (PA == 1) {
-            c = KeyOps<DT>::add(sk[r0], msuf) <= hik ? 1u : 0u;
+            c = KeyOps<DT>::add(sk(r0), msuf) <= hik ? 1u : 0u;
         } else {
-            uint32_t a0 = sk[r0];
-            if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk[n]), msuf) > hik) {
+            uint32_t a0 = sk(r0);
+            if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk(n)), msuf) > hik) {
                 c = 0;
             } else {
                 int lo1 = 1, hi1 = n;  // answer in [1, n]
                 while (lo1 < hi1) {
                     int mid = (lo1 + hi1 + 1) >> 1;
-                    if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk[n + mid - 1]), msuf) <= hik) lo1 = mid;
+                    if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk(n + mid - 1)), msuf) <= hik) lo1 = mid;
                     else hi1 = mid - 1;
                 }
                 c = (uint32_t)lo1;
@@ -478,7 +561,6 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
     uint8_t *qb = smem + L.q;
     uint32_t *D = (uint32_t *)(smem + L.tabD);
     uint8_t *rk = smem + L.rank;
-    uint32_t *sk = (uint32_t *)(smem + L.sk);
     uint8_t *sc = smem + L.sc;
     uint64_t *heap = (uint64_t *)(smem + L.heap);
     uint32_t *H = (uint32_t *)(smem + L.hash);
@@ -522,10 +604,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
             for (int r = lane; r < n; r += 32) {
                 uint32_t c = (uint32_t)tmp[r];
                 rk[p * n + c] = (uint8_t)r;
-                if (p < PA) {
-                    sk[p * n + r] = (uint32_t)(tmp[r] >> 32);
-                    sc[p * n + r] = (uint8_t)c;
-                }
+                if (p < PA) sc[p * n + r] = (uint8_t)c;
             }
             first_keys[p] = (uint32_t)(tmp[0] >> 32);
             last_keys[p] = (uint32_t)(tmp[n - 1] >> 32);
@@ -566,17 +645,25 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
         ws.width = 1u << 16;  // about 0.8% relative in float32 bit space
     }
     uint32_t bcur = 0, bcnt = 0;
-    uint32_t hsz = 0;       // heap size (lane 0's view is authoritative; broadcast below)
+    uint32_t wstart = 0, wcnt = 0;  // bridge window: batch entries [wstart, wstart + wcnt)
+    uint32_t wsize = 1;             // next window size: 1, 2, 4, ... 32 bridges
+    uint32_t hsz = 0;               // heap size (identical in every lane)
     uint32_t rlen = 0;
+    uint64_t rreg = ~0ull;          // result list in registers when k <= 32: lane l holds rank l
+    const bool rsmall = k <= 32;
     int t = 0;
     bool cap_err = false;
     int64_t maxq = 0;
     const int b = ix.b, R = ix.R;
+    int32_t *wref = (int32_t *)(smem + L.wref);
+    uint32_t *wkey = (uint32_t *)(smem + L.wkey);
 
     while (t < T) {
         if (bcur >= bcnt && !ws.exhausted) {
             bcnt = refill<DT>(ix, smem, L, ws, stats, cap_err);
             bcur = 0;
+            wstart = 0;
+            wcnt = 0;
             if (cap_err) break;
         }
         bool hb = bcur < bcnt;
@@ -586,21 +673,54 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
         uint64_t bc = hb ? bkey[bcur] : ~0ull;
         bool take_ref = hr && (!hb || (uint32_t)(top >> 32) <= (uint32_t)(bc >> 32));
         int32_t x = -1;
+        uint32_t xkey = 0;
+        bool have_key = false;
         int alen;
         if (take_ref) {
             uint32_t p = (uint32_t)top;
-            __syncwarp();
-            if (lane == 0) heap_pop(heap, hsz);
-            __syncwarp();
-            hsz = __shfl_sync(0xffffffffu, hsz, 0);
+            heap_pop(heap, hsz);
             alen = R;
             if (lane < R) x = __ldg(ix.G + (int64_t)p * R + lane);
             stats[ANN_STAT_REF_POPS]++;
         } else {
-            uint32_t j = bidx[bcur];
+            if (bcur >= wstart + wcnt) {
+                // fill the window: reference lists of the next bridges and their distances
+                wstart = bcur;
+                wcnt = min(wsize, bcnt - bcur);
+                if (wsize < 32) wsize <<= 1;
+                for (int e = lane; e < (int)wcnt * b; e += 32) {
+                    uint32_t j = bidx[wstart + e / b];
+                    int32_t r = __ldg(ix.brefs + (int64_t)j * b + (e % b));
+                    bool keep = r >= 0 && r < ix.N && !hash_has(H, L.hash_log, (uint32_t)r);
+                    wref[e] = keep ? r : -1;
+                }
+                __syncwarp();
+                int nc = 0;
+                for (int e0 = 0; e0 < (int)wcnt * b; e0 += 32) {
+                    int e = e0 + lane;
+                    bool keep = e < (int)wcnt * b && wref[e] >= 0;
+                    unsigned mk = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        int pos = nc + __popc(mk & ((1u << lane) - 1));
+                        cand[pos] = (uint32_t)wref[e];
+                        wkey[e] = (uint32_t)pos;  // temporarily: where its key will land
+                    }
+                    nc += __popc(mk);
+                }
+                __syncwarp();
+                cand_distances<DT>(ix, qb, cand, nc, ckey);
+                for (int e = lane; e < (int)wcnt * b; e += 32)
+                    if (wref[e] >= 0) wkey[e] = ckey[wkey[e]];
+                __syncwarp();
+            }
+            uint32_t wi = (bcur - wstart) * b;
             bcur++;
             alen = b;
-            if (lane < b) x = __ldg(ix.brefs + (int64_t)j * b + lane);
+            if (lane < b) {
+                x = wref[wi + lane];
+                xkey = wkey[wi + lane];
+            }
+            have_key = true;
             stats[ANN_STAT_BRIDGE_POPS]++;
         }
         bool isnew = lane < alen && x >= 0 && x < ix.N && !hash_has(H, L.hash_log, (uint32_t)x);
@@ -612,44 +732,56 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
         if ((mask >> lane) & 1u) {
             int pos = __popc(mask & ((1u << lane) - 1));
             cand[pos] = (uint32_t)x;
+            if (have_key) ckey[pos] = xkey;
             hash_add(H, L.hash_log, (uint32_t)x);
         }
         __syncwarp();
-        cand_distances<DT>(ix, qb, cand, m, ckey);
-        if (lane == 0) {
+        if (!have_key) cand_distances<DT>(ix, qb, cand, m, ckey);
+        uint64_t mine = lane < m ? (((uint64_t)ckey[lane] << 32) | cand[lane]) : ~0ull;
+        heap_push_batch(heap, hsz, mine, m);
+        if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
+        // result set: the k smallest by (key, id)
+        if (rsmall) {
+            for (int j = 0; j < m; j++) {
+                uint64_t e = __shfl_sync(0xffffffffu, mine, j);
+                if (k == 0) break;
+                uint64_t kth = __shfl_sync(0xffffffffu, rreg, k - 1);
+                if ((int)rlen == k && e >= kth) continue;
+                int pos = __popc(__ballot_sync(0xffffffffu, rreg < e));
+                uint64_t up = __shfl_up_sync(0xffffffffu, rreg, 1);
+                if (lane == pos) rreg = e;
+                else if (lane > pos) rreg = up;
+                if ((int)rlen < k) rlen++;
+            }
+        } else {
             for (int j = 0; j < m; j++) {
                 uint64_t e = ((uint64_t)ckey[j] << 32) | cand[j];
-                heap_push(heap, hsz, e);
-            }
-        }
-        __syncwarp();
-        hsz = __shfl_sync(0xffffffffu, hsz, 0);
-        if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
-        // result set: k smallest by (key, id), kept sorted in rbuf
-        for (int j = 0; j < m; j++) {
-            uint64_t e = ((uint64_t)ckey[j] << 32) | cand[j];
-            if (k == 0) break;
-            if ((int)rlen == k && e >= rbuf[k - 1]) continue;
-            // position = number of entries smaller than e
-            int cntless = 0;
-            for (int i = lane; i < (int)rlen; i += 32) cntless += rbuf[i] < e;
-            for (int off = 16; off > 0; off >>= 1) cntless += __shfl_xor_sync(0xffffffffu, cntless, off);
-            int newlen = (int)rlen < k ? (int)rlen + 1 : k;
-            // shift [cntless, newlen-1) up by one, top-down in chunks of 32
-            for (int top_i = newlen - 1; top_i > cntless; top_i -= 32) {
-                int i = top_i - lane;
-                uint64_t v = 0;
-                bool mv = i > cntless;
-                if (mv) v = rbuf[i - 1];
-                __syncwarp();
-                if (mv) rbuf[i] = v;
+                if ((int)rlen == k && e >= rbuf[k - 1]) continue;
+                // position = number of entries smaller than e
+                int cntless = 0;
+                for (int i = lane; i < (int)rlen; i += 32) cntless += rbuf[i] < e;
+                for (int off = 16; off > 0; off >>= 1) cntless += __shfl_xor_sync(0xffffffffu, cntless, off);
+                int newlen = (int)rlen < k ? (int)rlen + 1 : k;
+                // shift [cntless, newlen-1) up by one, top-down in chunks of 32
+                for (int top_i = newlen - 1; top_i > cntless; top_i -= 32) {
+                    int i = top_i - lane;
+                    uint64_t v = 0;
+                    bool mv = i > cntless;
+                    if (mv) v = rbuf[i - 1];
+                    __syncwarp();
+                    if (mv) rbuf[i] = v;
+                    __syncwarp();
+                }
+                if (lane == 0) rbuf[cntless] = e;
+                rlen = (uint32_t)newlen;
                 __syncwarp();
             }
-            if (lane == 0) rbuf[cntless] = e;
-            rlen = (uint32_t)newlen;
-            __syncwarp();
         }
         t += m;
+    }
+    if (rsmall) {
+        if (lane < k) rbuf[lane] = rreg;
+        __syncwarp();
     }
     stats[ANN_STAT_DISCOVERED] = t;
     stats[ANN_STAT_MAX_Q] = maxq;
@@ -672,7 +804,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
 }
 
 template <int DT>
-__global__ void __launch_bounds__(512) search_kernel(SearchArgs A) {
+__global__ void __launch_bounds__(256, 2) search_kernel(SearchArgs A) {
     extern __shared__ __align__(16) uint8_t smem_all[];
     const int warp = threadIdx.x >> 5;
     uint8_t *smem = smem_all + (size_t)warp * A.L.total;
@@ -724,8 +856,8 @@ struct Tune {
 // the per-warp shared-memory slice (ties go to more warps per CTA).
 static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     Tune t;
-    t.bcap = 256;
-    WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap);
+    t.bcap = 128;
+    WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
     int best_w = 1, best_res = 0;
@@ -751,7 +883,7 @@ static int launch_search(const SearchArgs &base, int capT, cudaStream_t stream, 
     A.capT = capT;
     Tune tn = choose_tune(A.ix, capT, A.kmax);
     A.bcap = tn.bcap;
-    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap);
+    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b);
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
