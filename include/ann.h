@@ -164,7 +164,7 @@ enum {
     ANN_STAT_WALK_NODES,     /* prefix nodes read by those walks */
     ANN_STAT_WALK_LEAVES,    /* leaf entries read by those walks */
     ANN_STAT_MAX_Q,          /* largest main-queue length */
-    ANN_STAT_RESERVED,
+    ANN_STAT_PRELOADED,      /* reference pops whose kNN row was loaded during the previous step */
     ANN_NSTATS
 };
 

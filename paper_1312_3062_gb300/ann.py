@@ -19,7 +19,7 @@ ANN_OK, ANN_PENDING = 0, 1
 ANN_ERR_ARG, ANN_ERR_OOM, ANN_ERR_CAPACITY, ANN_ERR_TIMEOUT, ANN_ERR_CUDA, ANN_ERR_FORMAT = -1, -2, -3, -4, -5, -6
 ANN_MODE_PLAIN, ANN_MODE_PERSISTENT = 0, 1
 STAT_NAMES = ("discovered", "ref_pops", "bridge_pops", "walks", "walk_nodes", "walk_leaves", "max_q",
-              "reserved")
+              "preloaded")
 ANN_NSTATS = len(STAT_NAMES)
 
 if not os.path.exists(_build.LIB):

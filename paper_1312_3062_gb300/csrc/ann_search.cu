@@ -138,34 +138,43 @@ __device__ __forceinline__ void hash_add(uint32_t *H, uint32_t log, uint32_t x) 
 // shuffles; a push appends and sifts up (rarely more than one level).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void warp_argmin(uint64_t &v, uint32_t &i) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        uint64_t ov = __shfl_xor_sync(0xffffffffu, v, off);
-        uint32_t oi = __shfl_xor_sync(0xffffffffu, i, off);
-        if (ov < v || (ov == v && oi < i)) {
-            v = ov;
-            i = oi;
-        }
-    }
+    // composite minimum with two warp reductions (key part, then id part)
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    const uint32_t mh = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+    const unsigned who = __ballot_sync(0xffffffffu, hi == mh && lo == ml);
+    i = __shfl_sync(0xffffffffu, i, __ffs(who) - 1);
+    v = ((uint64_t)mh << 32) | ml;
 }
 
-// append m entries (lane j holds entry j, j < m) and restore the heap order
+// append m entries (lane j holds entry j, j < m) and restore the heap order:
+// every new entry checks its parent in parallel; only those smaller than
+// their parent sift up, one after another (values on a sift-up path only
+// decrease, so entries that passed the check stay valid)
 __device__ __forceinline__ void heap_push_batch(uint64_t *h, uint32_t &sz, uint64_t e, int m) {
     const int lane = lane_id();
-    if (lane < m) h[sz + lane] = e;
+    const uint32_t pos = sz + lane;
+    if (lane < m) h[pos] = e;
     __syncwarp();
-    if (lane == 0) {
-        for (int j = 0; j < m; j++) {
-            uint32_t i = sz + j;
-            uint64_t v = h[i];
-            while (i > 0) {
-                uint32_t p = (i - 1) >> 5;
-                uint64_t pv = h[p];
-                if (pv <= v) break;
-                h[i] = pv;
-                i = p;
+    bool need = lane < m && pos > 0 && h[(pos - 1) >> 5] > e;
+    unsigned nm = __ballot_sync(0xffffffffu, need);
+    if (nm) {
+        __syncwarp();
+        if (lane == 0) {
+            while (nm) {
+                int j = __ffs(nm) - 1;
+                nm &= nm - 1;
+                uint32_t i = sz + j;
+                uint64_t v = h[i];
+                while (i > 0) {
+                    uint32_t p = (i - 1) >> 5;
+                    uint64_t pv = h[p];
+                    if (pv <= v) break;
+                    h[i] = pv;
+                    i = p;
+                }
+                h[i] = v;
             }
-            h[i] = v;
         }
     }
     sz += m;
@@ -657,6 +666,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
     const int b = ix.b, R = ix.R;
     int32_t *wref = (int32_t *)(smem + L.wref);
     uint32_t *wkey = (uint32_t *)(smem + L.wkey);
+    uint32_t pre_id = 0xffffffffu;  // reference whose kNN row is already in `pre_row`
+    int32_t pre_row = -1;
 
     while (t < T) {
         if (bcur >= bcnt && !ws.exhausted) {
@@ -680,7 +691,13 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
             uint32_t p = (uint32_t)top;
             heap_pop(heap, hsz);
             alen = R;
-            if (lane < R) x = __ldg(ix.G + (int64_t)p * R + lane);
+            if (p == pre_id) {
+                x = pre_row;
+                stats[ANN_STAT_PRELOADED]++;
+            } else if (lane < R) {
+                x = __ldg(ix.G + (int64_t)p * R + lane);
+            }
+            pre_id = 0xffffffffu;
             stats[ANN_STAT_REF_POPS]++;
         } else {
             if (bcur >= wstart + wcnt) {
@@ -740,18 +757,33 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
         uint64_t mine = lane < m ? (((uint64_t)ckey[lane] << 32) | cand[lane]) : ~0ull;
         heap_push_batch(heap, hsz, mine, m);
         if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
+        // The next pop is known now: when it is a reference, start loading its
+        // kNN row so that the load overlaps the result-set update below.
+        if (t + m < T && hsz > 0) {
+            uint64_t ntop = heap[0];
+            bool next_ref = bcur >= bcnt ? (ws.exhausted || true) : (uint32_t)(ntop >> 32) <= (uint32_t)(bkey[bcur] >> 32);
+            if (next_ref) {
+                pre_id = (uint32_t)ntop;
+                pre_row = lane < R ? __ldg(ix.G + (int64_t)pre_id * R + lane) : -1;
+            }
+        }
         // result set: the k smallest by (key, id)
         if (rsmall) {
-            for (int j = 0; j < m; j++) {
-                uint64_t e = __shfl_sync(0xffffffffu, mine, j);
-                if (k == 0) break;
-                uint64_t kth = __shfl_sync(0xffffffffu, rreg, k - 1);
-                if ((int)rlen == k && e >= kth) continue;
-                int pos = __popc(__ballot_sync(0xffffffffu, rreg < e));
-                uint64_t up = __shfl_up_sync(0xffffffffu, rreg, 1);
-                if (lane == pos) rreg = e;
-                else if (lane > pos) rreg = up;
-                if ((int)rlen < k) rlen++;
+            if (k > 0) {
+                uint64_t kth = __shfl_sync(0xffffffffu, rreg, k - 1);  // ~0 while fewer than k
+                unsigned pm = __ballot_sync(0xffffffffu, lane < m && mine < kth);
+                while (pm) {
+                    int j = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    uint64_t e = __shfl_sync(0xffffffffu, mine, j);
+                    kth = __shfl_sync(0xffffffffu, rreg, k - 1);
+                    if (e >= kth) continue;
+                    int pos = __popc(__ballot_sync(0xffffffffu, rreg < e));
+                    uint64_t up = __shfl_up_sync(0xffffffffu, rreg, 1);
+                    if (lane == pos) rreg = e;
+                    else if (lane > pos) rreg = up;
+                    if ((int)rlen < k) rlen++;
+                }
             }
         } else {
             for (int j = 0; j < m; j++) {
