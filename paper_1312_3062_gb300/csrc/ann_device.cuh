@@ -70,6 +70,44 @@ __device__ inline void warp_sort_pairs(uint64_t *keys, uint32_t *vals, int L) {
     }
 }
 
+// Bitonic sort of 32*EPL keys held in registers, ascending in the blocked
+// order (element i = lane*EPL + slot).  Pairs in different lanes exchange
+// through shuffles; pairs in the same lane swap registers.
+template <int EPL>
+__device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
+    const int lane = lane_id();
+    constexpr int L = 32 * EPL;
+#pragma unroll
+    for (int k = 2; k <= L; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= EPL) {
+#pragma unroll
+                for (int s = 0; s < EPL; s++) {
+                    const int i = lane * EPL + s;
+                    const uint64_t o = __shfl_xor_sync(0xffffffffu, v[s], j / EPL);
+                    const bool up = (i & k) == 0, lower = (i & j) == 0;
+                    const uint64_t mn = v[s] < o ? v[s] : o, mx = v[s] < o ? o : v[s];
+                    v[s] = (lower == up) ? mn : mx;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < EPL; s++) {
+                    const int p = s ^ j;
+                    if (p > s) {
+                        const bool up = ((lane * EPL + s) & k) == 0;
+                        const uint64_t a = v[s], b = v[p];
+                        if ((a > b) == up) {
+                            v[s] = b;
+                            v[p] = a;
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // per-part key of one part of the query against one center, computed by one lane
 // ---------------------------------------------------------------------------

@@ -545,6 +545,36 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
     return 0;
 }
 
+// Sort part p by (key, center id) in registers; write each center's rank and,
+// for prefix parts, the center id at each rank; record the first/last key.
+template <int EPL>
+__device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_t *sc, int p, int n, int PA,
+                                          uint32_t *first_keys, uint32_t *last_keys) {
+    const int lane = lane_id();
+    uint64_t v[EPL];
+#pragma unroll
+    for (int s = 0; s < EPL; s++) {
+        const int c = lane * EPL + s;
+        v[s] = c < n ? (((uint64_t)D[p * n + c]) << 32) | (uint32_t)c : ~0ull;
+    }
+    reg_bitonic_sort<EPL>(v);
+#pragma unroll
+    for (int s = 0; s < EPL; s++) {
+        const int r = lane * EPL + s;
+        if (r < n) {
+            const uint32_t c = (uint32_t)v[s];
+            rk[p * n + c] = (uint8_t)r;
+            if (p < PA) sc[p * n + r] = (uint8_t)c;
+        }
+    }
+    first_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> 32);
+    uint64_t lastv = v[0];
+#pragma unroll
+    for (int s = 0; s < EPL; s++)
+        if (s == (n - 1) % EPL) lastv = v[s];
+    last_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, lastv, (n - 1) / EPL) >> 32);
+}
+
 // ---------------------------------------------------------------------------
 // one query, one warp
 // ---------------------------------------------------------------------------
@@ -601,24 +631,14 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
     uint32_t msuf = 0;
     uint32_t kmin = 0, kmaxall = 0;
     {
-        uint64_t *tmp = heap;  // heap is empty until the main loop
-        int Lp = 1;
-        while (Lp < n) Lp <<= 1;
         uint32_t first_keys[kMaxP], last_keys[kMaxP];
         for (int p = 0; p < P; p++) {
-            for (int i = lane; i < Lp; i += 32)
-                tmp[i] = i < n ? (((uint64_t)D[p * n + i]) << 32) | (uint32_t)i : ~0ull;
-            __syncwarp();
-            warp_sort_pairs(tmp, nullptr, Lp);
-            for (int r = lane; r < n; r += 32) {
-                uint32_t c = (uint32_t)tmp[r];
-                rk[p * n + c] = (uint8_t)r;
-                if (p < PA) sc[p * n + r] = (uint8_t)c;
-            }
-            first_keys[p] = (uint32_t)(tmp[0] >> 32);
-            last_keys[p] = (uint32_t)(tmp[n - 1] >> 32);
-            __syncwarp();
+            if (n <= 32) sort_part<1>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 64) sort_part<2>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 128) sort_part<4>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else sort_part<8>(D, rk, sc, p, n, PA, first_keys, last_keys);
         }
+        __syncwarp();
         // smallest / largest bridge keys and the min-suffix sum, grouped (D0+D1)+(D2+...)
         auto group_sum = [&](const uint32_t *v) -> uint32_t {
             uint32_t a = KeyOps<DT>::add(v[0], v[1]);
