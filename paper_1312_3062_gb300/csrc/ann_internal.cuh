@@ -78,6 +78,13 @@ struct ann_index {
 namespace ann {
 // implemented in ann_search.cu
 void free_plans(ann_index *ix);
+// plain launch of Algorithm 1 sized for a budget capT known on the host (no sync)
+int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
+                        int32_t kmax, int capT, int32_t *out_ids, void *out_keys, int32_t *out_status,
+                        cudaStream_t stream);
+// implemented in ann_knn_tc.cu: exact k-NN of uint8 rows on the tensor cores, d in {64, 128}, k <= 32
+int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_t nq, int d, int k,
+                  int exclude_self, int32_t *out_ids, uint32_t *out_keys, cudaStream_t s);
 // implemented in ann_index.cu
 int build_bridge_index_from_host(ann_index *ix, int64_t M, const uint64_t *ids,
                                  const int64_t *offsets, const int32_t *refs);

@@ -1052,6 +1052,27 @@ static int record_persistent(const SearchArgs &A, int64_t nq, const int32_t *T, 
     return ANN_OK;
 }
 
+int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
+                        int32_t kmax, int capT, int32_t *out_ids, void *out_keys, int32_t *out_status,
+                        cudaStream_t stream) {
+    int r = device_props();
+    if (r != ANN_OK) return r;
+    if (nq == 0) return ANN_OK;
+    SearchArgs A{};
+    A.ix = ix->dev;
+    A.queries = queries;
+    A.nq = nq;
+    A.k = k;
+    A.T = T;
+    A.kmax = kmax;
+    A.out_ids = out_ids;
+    A.out_keys = out_keys;
+    A.out_status = out_status;
+    if (capT > kMaxT) capT = kMaxT;
+    if (capT < 32) capT = 32;
+    return launch_search(A, capT, stream, false, nullptr, nullptr, nq, nullptr);
+}
+
 }  // namespace ann
 
 using namespace ann;

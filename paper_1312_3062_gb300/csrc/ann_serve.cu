@@ -141,6 +141,9 @@ static bool launch_batch(ann_server *S, Slot &sl, std::vector<std::shared_ptr<Re
     int32_t *hk = (int32_t *)(h + (size_t)kServeMaxBatch * vb);
     int32_t *hT = hk + kServeMaxBatch;
     int32_t at = 0;
+    int32_t capT = 0;
+    for (auto &r : batch)
+        for (int32_t v : r->T) capT = std::max(capT, v);
     for (auto &r : batch) {
         memcpy(h + qo, r->queries.data(), (size_t)r->nq * vb);
         qo += (size_t)r->nq * vb;
@@ -163,8 +166,7 @@ static bool launch_batch(ann_server *S, Slot &sl, std::vector<std::shared_ptr<Re
               cudaMemcpyAsync(dk, hk, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaMemcpyAsync(dT, hT, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess;
     if (ok)
-        ok = ann_search_batch(S->index, dq, nq, dk, dT, 0, 0, kmax, ANN_MODE_PLAIN, dids, dkeys, dst, nullptr, s) ==
-             ANN_OK;
+        ok = search_launch_plain(S->index, dq, nq, dk, dT, kmax, capT, dids, dkeys, dst, s) == ANN_OK;
     uint8_t *ho = sl.h_out;
     if (ok)
         ok = cudaMemcpyAsync(ho, dids, (size_t)nq * kmax * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
