@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int half = ew >> 2;             // column half
         const int row = quad * 32 + lane;     // row of the block
         uint64_t *mylist = lists + ((size_t)ew * 32 + lane) * k;
-        uint32_t *myrn = rn_s + ew * (BN / 2);
+        float *myrn = (float *)(rn_s + ew * (BN / 2));
         int64_t u = 0;
         for (int64_t blk = blockIdx.x; blk < nblocks && !*err; blk += gridDim.x) {
             const int64_t qrow = blk * BM + row;
@@ -295,15 +295,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const float qn = valid_row ? (float)prm.qnorm[qrow] : 0.f;
             for (int i = 0; i < k; i++) mylist[i] = ~0ull;
             uint64_t thr = ~0ull;             // current k-th entry of this list
-            float thr_f = 3.0e38f;
+            float thr_f = 1.0e20f;            // above every key (keys are below 2^25)
             bool ok = true;
             for (int64_t t = 0; t < ntiles; t++, u++) {
                 const int acc = (int)(u & 1);
-                // reference norms of this tile's column half (padding: a key no list accepts)
+                // reference norms of this tile's column half as floats (exact below 2^24);
+                // padding rows get a key no list accepts
                 const int64_t r0 = t * BN;
                 for (int c = lane; c < BN / 2; c += 32) {
                     const int64_t rid = r0 + half * (BN / 2) + c;
-                    myrn[c] = rid < prm.N ? prm.rnorm[rid] : 0x7F000000u;
+                    myrn[c] = rid < prm.N ? (float)prm.rnorm[rid] : 1.0e30f;
                 }
                 __syncwarp();
                 if (!mbar_wait(&tfull[acc], (uint32_t)((u >> 1) & 1), err)) {
@@ -316,11 +317,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     uint32_t v[32];
                     __syncwarp();
                     tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * BN + col0), v);
-                    if (valid_row) {
+                    // 32 exact keys without branches; the list is touched only when one beats its k-th entry
+                    float kk[32];
+                    float mn = 1.0e30f;
+#pragma unroll
+                    for (int j4 = 0; j4 < 8; j4++) {
+                        const float4 r4 = *(const float4 *)(myrn + cb + 4 * j4);
+                        const float rr[4] = {r4.x, r4.y, r4.z, r4.w};
+#pragma unroll
+                        for (int q = 0; q < 4; q++) {
+                            const int j = 4 * j4 + q;
+                            kk[j] = __fmaf_rn(-2.0f, __uint_as_float(v[j]), qn + rr[q]);
+                            mn = fminf(mn, kk[j]);
+                        }
+                    }
+                    if (valid_row && mn <= thr_f) {
 #pragma unroll
                         for (int j = 0; j < 32; j++) {
-                            const float dot = __uint_as_float(v[j]);
-                            const float kf = __fmaf_rn(-2.0f, dot, qn + (float)myrn[cb + j]);
+                            const float kf = kk[j];
                             if (kf <= thr_f) {
                                 const int64_t rid = r0 + col0 + j;
                                 if (rid < prm.N && !(prm.exclude_self && rid == qrow)) {
@@ -333,7 +347,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                                         }
                                         mylist[p] = e;
                                         thr = mylist[k - 1];
-                                        thr_f = thr == ~0ull ? 3.0e38f : (float)(uint32_t)(thr >> 32);
+                                        thr_f = thr == ~0ull ? 1.0e20f : (float)(uint32_t)(thr >> 32);
                                     }
                                 }
                             }
