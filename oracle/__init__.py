@@ -169,6 +169,8 @@ def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int, nthreads: i
 def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, queries: np.ndarray,
            k, T, kmax: int | None = None, nthreads: int = 1, trace: bool = False):
     """Algorithm 1 for each query.  k, T: scalars or per-query arrays.
+    graph: (N, R) int32 rows, or an int R to compute each popped row on demand
+    (its R nearest other references by linear scan).
 
     Returns (ids (nq, kmax) int32, keys (nq, kmax) float64, stats dict of arrays);
     with trace=True the stats dict also holds 'trace' (nq, max T): the
@@ -176,7 +178,11 @@ def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, quer
     lib = _load()
     X = np.ascontiguousarray(X)
     queries = np.ascontiguousarray(queries)
-    graph = np.ascontiguousarray(graph, dtype=np.int32)
+    if isinstance(graph, (int, np.integer)):
+        R_on_demand = int(graph)      # rows computed on demand by linear scan
+        graph = None
+    else:
+        graph = np.ascontiguousarray(graph, dtype=np.int32)
     centers = np.ascontiguousarray(centers)
     assert X.dtype == queries.dtype == centers.dtype
     N, d = X.shape
@@ -195,7 +201,8 @@ def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, quer
     refs = np.ascontiguousarray(bg["refs"], dtype=np.int32)
     cap = int(T.max()) if (trace and nq) else 0
     disc = np.empty((nq, max(cap, 1)), np.int32)
-    rc = lib.oracle_search(_ptr(X), N, d, _dtype_code(X), _ptr(graph), graph.shape[1], P, n,
+    rc = lib.oracle_search(_ptr(X), N, d, _dtype_code(X), None if graph is None else _ptr(graph),
+                           R_on_demand if graph is None else graph.shape[1], P, n,
                            _ptr(centers), len(bridges), _ptr(bridges), _ptr(offs), _ptr(refs),
                            _ptr(queries), nq, _ptr(k), _ptr(T), kmax, _ptr(ids), _ptr(keys),
                            _ptr(st), _ptr(disc) if trace else None, cap, nthreads)

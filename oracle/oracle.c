@@ -715,6 +715,9 @@ static void search_one(const index_t *ix, const void *q, int k, int T, int kmax,
         pq_push(&Q, it);
     }
     int64_t t = 0;
+    int32_t rowbuf[64];
+    double rowk[64];
+    int64_t rowi[64];
     if (Q.len > st[ST_MAX_Q]) st[ST_MAX_Q] = Q.len;
     while (Q.len > 0 && t < T) {
         q_item p = pq_pop(&Q);
@@ -722,7 +725,21 @@ static void search_one(const index_t *ix, const void *q, int k, int T, int kmax,
         int64_t alen;
         if (p.kind == 0) {
             st[ST_REF_POPS]++;
-            adj = ix->graph + p.id * ix->R;
+            if (ix->graph) {
+                adj = ix->graph + p.id * ix->R;
+            } else {
+                /* no stored graph: Adj[p] by its definition, the R nearest
+                   other references by linear scan (Sec. 3.1) */
+                int len = 0;
+                for (int64_t j = 0; j < ix->N; j++) {
+                    if (j == p.id) continue;
+                    double kj = sqdist(row_ptr(ix->X, p.id, ix->d, ix->dtype), row_ptr(ix->X, j, ix->d, ix->dtype),
+                                       ix->d, ix->dtype);
+                    topk_insert(rowk, rowi, &len, ix->R, kj, j);
+                }
+                for (int r = 0; r < ix->R; r++) rowbuf[r] = r < len ? (int32_t)rowi[r] : -1;
+                adj = rowbuf;
+            }
             alen = ix->R;
         } else {
             st[ST_BRIDGE_POPS]++;
@@ -803,6 +820,8 @@ static void *worker(void *arg) {
 }
 
 /* Batched search: one query at a time per thread (nthreads >= 1).
+   graph may be NULL: then each popped reference's R nearest neighbours are
+   computed on demand by linear scan.
    k[i], T[i]: per-query result count (<= kmax) and budget.
    bridges/boff/brefs: the bridge graph as produced by oracle_bridge_graph.
    disc (optional, nq*disc_cap): discovered ids in discovery order, -1 after. */
@@ -811,7 +830,7 @@ int oracle_search(const void *X, int64_t N, int d, int dtype, const int32_t *gra
                   const int64_t *boff, const int32_t *brefs, const void *queries, int64_t nq,
                   const int32_t *k, const int32_t *T, int kmax, int32_t *out_ids,
                   double *out_keys, int64_t *stats, int32_t *disc, int disc_cap, int nthreads) {
-    if (P > MAXP || P < 1 || d % P != 0) return -1;
+    if (P > MAXP || P < 1 || d % P != 0 || R > 64) return -1;
     index_t ix = {X, N, d, dtype, graph, R, P, n, centers, M, bridges, boff, brefs};
     job_t job = {&ix, queries, nq, k, T, kmax, out_ids, out_keys, stats, disc, disc_cap, 0,
                  PTHREAD_MUTEX_INITIALIZER};

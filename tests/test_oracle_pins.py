@@ -478,3 +478,14 @@ def test_recall_counts_ties_at_kth(oracle_lib):
     assert oracle.recall_at_k(found, true_keys, X, q, 2)[0] == 1.0
     found = np.array([[0, 3]], np.int32)
     assert oracle.recall_at_k(found, true_keys, X, q, 2)[0] == 0.5
+
+
+def test_on_demand_rows_equal_stored_graph(oracle_lib):
+    # Adj[x] computed by linear scan when popped = the stored exact R-NN row
+    rng = np.random.default_rng(35)
+    X, G, C, bg = tiny_index(rng, 300, 16, 2, 6, 7, 10, 3, np.uint8)
+    Qs = gmm(rng, 6, 16, 6, 20.0, np.uint8)
+    a = oracle.search(X, G, C, bg, Qs, 5, 120, trace=True)
+    b = oracle.search(X, 7, C, bg, Qs, 5, 120, trace=True)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[2]["trace"], b[2]["trace"])
