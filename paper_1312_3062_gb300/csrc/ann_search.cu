@@ -225,6 +225,53 @@ __device__ void cand_distances(const DevIndex &ix, const uint8_t *qbytes, const 
     int rounds_per_batch = MAXL / cpl;
     if (rounds_per_batch < 1) rounds_per_batch = 1;
     const uint4 *qv = (const uint4 *)qbytes;
+    if (cpl == 1 && G == nc) {
+        // fast path: one 16-byte chunk per lane per row, MAXL rows' loads in flight
+        const uint4 q = qv[lig];
+        for (int base = 0; base < m; base += per_round * MAXL) {
+            uint4 buf[MAXL];
+#pragma unroll
+            for (int u = 0; u < MAXL; u++) {
+                const int j = base + u * per_round + grp;
+                if (j < m) buf[u] = __ldg((const uint4 *)((const uint8_t *)ix.X + (int64_t)cand[j] * vb) + lig);
+            }
+#pragma unroll
+            for (int u = 0; u < MAXL; u++) {
+                const int j = base + u * per_round + grp;
+                uint32_t acc = 0;
+                float hi = 0.f, lo = 0.f;
+                if (j < m) {
+                    const uint4 a = buf[u];
+                    if (DT == ANN_U8) {
+                        uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
+                        uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
+                        acc = __dp4a(d0, d0, acc);
+                        acc = __dp4a(d1, d1, acc);
+                        acc = __dp4a(d2, d2, acc);
+                        acc = __dp4a(d3, d3, acc);
+                    } else {
+                        df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
+                        df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
+                    }
+                }
+                for (int off = G >> 1; off > 0; off >>= 1) {
+                    if (DT == ANN_U8) {
+                        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                    } else {
+                        float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                        float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                        df_add(hi, lo, h2, l2);
+                    }
+                }
+                if (j < m && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
+            }
+            if (base + per_round * MAXL >= m) break;
+        }
+        __syncwarp();
+        return;
+    }
     for (int base = 0; base < m; base += per_round * rounds_per_batch) {
         uint4 buf[MAXL];
         // issue every load of this batch
@@ -856,7 +903,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
 }
 
 template <int DT>
-__global__ void __launch_bounds__(256, 2) search_kernel(SearchArgs A) {
+__global__ void __launch_bounds__(192, 2) search_kernel(SearchArgs A) {
     extern __shared__ __align__(16) uint8_t smem_all[];
     const int warp = threadIdx.x >> 5;
     uint8_t *smem = smem_all + (size_t)warp * A.L.total;
@@ -912,12 +959,21 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
+    // register-file limit of the kernel (both instantiations use the same budget)
+    static int regs = 0;
+    if (!regs) {
+        cudaFuncAttributes fa;
+        regs = cudaFuncGetAttributes(&fa, search_kernel<ANN_U8>) == cudaSuccess ? fa.numRegs : 168;
+        if (regs < 32) regs = 32;
+    }
+    const int warps_by_regs = 65536 / (regs * 32);
     int best_w = 1, best_res = 0;
-    for (int w = 1; w <= 8; w++) {
+    for (int w = 1; w <= 6; w++) {
         size_t cta = (size_t)w * L.total;
         if (cta > budget) break;
         int ctas = (int)(per_sm / (cta + per_cta_reserved));
         if (ctas > 32 / w) ctas = 32 / w;
+        if (ctas > warps_by_regs / w) ctas = warps_by_regs / w;
         int res = ctas * w;
         if (res >= best_res) {
             best_res = res;
