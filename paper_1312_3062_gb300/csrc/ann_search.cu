@@ -104,6 +104,10 @@ struct SearchArgs {
     int capT;
     int bcap;
     WarpLayout L;
+    // per-warp global scratch for sorted bridge windows (large-budget kernels):
+    // gcap x (2 keys + 2 values)
+    uint8_t *gscratch;
+    uint32_t gcap;
 };
 
 // ---------------------------------------------------------------------------
@@ -355,6 +359,8 @@ struct WalkState {
     bool exhausted;   // all non-empty bridges produced
     uint32_t width;   // window width in key units (u8) or key-bit units (f32)
     uint32_t kmin, kmaxall, msuf;
+    uint32_t gpos, gcnt;  // sorted window in global scratch: next entry, entries
+    int gbuf;             // which of the two scratch buffers holds it
 };
 
 // Emit the composite (key << 32 | packed ranks) of every non-empty bridge with
@@ -365,7 +371,8 @@ struct WalkState {
 // are processed as one flat range, 32 consecutive leaves per step.
 template <int DT>
 __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
-                         uint64_t hi, int64_t *st_nodes, int64_t *st_leaves) {
+                         uint64_t hi, int64_t *st_nodes, int64_t *st_leaves, uint64_t *okey, uint32_t *oval,
+                         uint32_t ocap) {
     const int lane = lane_id();
     const int n = ix.n, P = ix.P, PA = ix.PA;
     const uint32_t *D = (const uint32_t *)(smem + L.tabD);
@@ -378,6 +385,8 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     uint32_t *bidx = (uint32_t *)(smem + L.bidx);
     uint32_t *cnt = (uint32_t *)(smem + L.misc);
     const uint32_t hik = (uint32_t)(hi >> 32);
+    const bool pow2n = (n & (n - 1)) == 0;
+    const int logn = 31 - __clz(n);
     const uint32_t msuf = cnt[3];  // min-suffix key sum, stored by the caller
     const int nsuf = P - PA;
     if (lane == 0) cnt[0] = 0;
@@ -488,23 +497,26 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                 while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
                 uint32_t j = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
                 uint32_t lf = __ldg(ix.leaf + j);
-                uint32_t ksuf, rsuf;
+                // key first; the rank lookups only for keys inside the window
+                uint32_t c2 = 0, c3 = lf, ksuf;
                 if (nsuf == 1) {
                     ksuf = D[(P - 1) * n + lf];
-                    rsuf = rk[(P - 1) * n + lf];
                 } else {
-                    uint32_t c2 = lf / n, c3 = lf - (lf / n) * n;
+                    c2 = pow2n ? (lf >> logn) : lf / n;
+                    c3 = lf - c2 * n;
                     ksuf = KeyOps<DT>::add(D[2 * n + c2], D[3 * n + c3]);
-                    rsuf = ((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3];
                 }
                 uint32_t key = KeyOps<DT>::add(nodes[4 * np + 2], ksuf);
+                if (key > hik || (!first && key < (uint32_t)(lo >> 32))) continue;
+                uint32_t rsuf = nsuf == 1 ? (uint32_t)rk[(P - 1) * n + lf]
+                                          : (((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3]);
                 uint32_t ranks = (nodes[4 * np + 3] << (8 * nsuf)) | rsuf;
                 uint64_t comp = ((uint64_t)key << 32) | ranks;
                 if (comp <= hi && (first || comp > lo)) {
                     uint32_t s = atomicAdd(&cnt[0], 1u);
-                    if (s < L.bcap) {
-                        bkey[s] = comp;
-                        bidx[s] = j;
+                    if (s < ocap) {
+                        okey[s] = comp;
+                        oval[s] = j;
                     }
                 }
             }
@@ -542,7 +554,7 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
     while (!ws.exhausted) {
         uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
         uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, &stats[ANN_STAT_WALK_NODES],
-                              &stats[ANN_STAT_WALK_LEAVES]);
+                              &stats[ANN_STAT_WALK_LEAVES], bkey, bidx, L.bcap);
         stats[ANN_STAT_WALKS]++;
         if (c > L.bcap) {
             // too many in the window: halve it (in composite space)
@@ -558,7 +570,7 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
             uint64_t h2 = base + span / 2;
             while (true) {
                 c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, &stats[ANN_STAT_WALK_NODES],
-                             &stats[ANN_STAT_WALK_LEAVES]);
+                             &stats[ANN_STAT_WALK_LEAVES], bkey, bidx, L.bcap);
                 stats[ANN_STAT_WALKS]++;
                 if (c <= L.bcap) break;
                 span = h2 - base;
@@ -590,6 +602,153 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
         return c;
     }
     return 0;
+}
+
+// Stable LSD radix sort of n (composite, index) pairs held in global scratch
+// by one warp: 8-bit digits, passes whose digit is the same for every entry
+// are skipped.  Returns the buffer (0 or 1) that holds the result.  cnt256:
+// 256 shared-memory counters.
+__device__ int warp_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, uint32_t n,
+                               uint32_t *cnt256) {
+    const int lane = lane_id();
+    int cur = 0;
+    for (int pass = 0; pass < 8; pass++) {
+        const int sh = 8 * pass;
+        uint64_t *ks = cur ? k1 : k0;
+        uint32_t *vs = cur ? v1 : v0;
+        uint64_t *kd = cur ? k0 : k1;
+        uint32_t *vd = cur ? v0 : v1;
+        for (int i = lane; i < 256; i += 32) cnt256[i] = 0;
+        __syncwarp();
+        for (uint32_t i = lane; i < n; i += 32) atomicAdd(&cnt256[(ks[i] >> sh) & 255], 1u);
+        __syncwarp();
+        // skip a pass whose digit is identical for all entries
+        bool all_same = false;
+        for (int i = lane; i < 256; i += 32) all_same |= cnt256[i] == n;
+        if (__any_sync(0xffffffffu, all_same)) continue;
+        // exclusive scan of the 256 counters (8 per lane)
+        uint32_t loc[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            loc[i] = cnt256[lane * 8 + i];
+            sum += loc[i];
+        }
+        uint32_t incl = sum;
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += v;
+        }
+        uint32_t run = incl - sum;
+        __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            cnt256[lane * 8 + i] = run;
+            run += loc[i];
+        }
+        __syncwarp();
+        // stable scatter, 32 entries at a time in input order
+        for (uint32_t c0 = 0; c0 < n; c0 += 32) {
+            const uint32_t i = c0 + lane;
+            const bool valid = i < n;
+            const uint64_t kv = valid ? ks[i] : 0;
+            const uint32_t vv = valid ? vs[i] : 0;
+            const uint32_t dig = valid ? (uint32_t)((kv >> sh) & 255) : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, dig);
+            const int rank = __popc(peers & ((1u << lane) - 1));
+            const uint32_t base = valid ? cnt256[dig] : 0;
+            if (valid) {
+                kd[base + rank] = kv;
+                vd[base + rank] = vv;
+            }
+            __syncwarp();
+            if (valid && rank == 0) cnt256[dig] = base + __popc(peers);
+            __syncwarp();
+        }
+        cur ^= 1;
+    }
+    __syncwarp();
+    return cur;
+}
+
+// Refill the shared-memory batch with the next bridges after ws.lo in order.
+// A walk emits every non-empty bridge of a key window into the warp's global
+// scratch (up to gcap), the window is sorted once, and the batch is served
+// from it bcap entries at a time.  Returns the count (0 = none left).
+template <int DT>
+__device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, WalkState &ws,
+                           int64_t *stats, bool &cap_err, uint8_t *wscratch, uint32_t gcap) {
+    uint64_t *gk0 = (uint64_t *)wscratch;
+    uint64_t *gk1 = gk0 + gcap;
+    uint32_t *gv0 = (uint32_t *)(gk1 + gcap);
+    uint32_t *gv1 = gv0 + gcap;
+    uint64_t *bkey = (uint64_t *)(smem + L.bkey);
+    uint32_t *bidx = (uint32_t *)(smem + L.bidx);
+    const int lane = lane_id();
+    if (ws.gpos >= ws.gcnt) {
+        ws.gpos = ws.gcnt = 0;
+        while (!ws.exhausted) {
+            uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
+            uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, &stats[ANN_STAT_WALK_NODES],
+                                  &stats[ANN_STAT_WALK_LEAVES], gk0, gv0, gcap);
+            stats[ANN_STAT_WALKS]++;
+            if (c > gcap) {
+                // too many in the window: halve it (in composite space)
+                uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
+                uint64_t span = hi - base;
+                if (span == 0) { cap_err = true; return 0; }
+                if (ws.width > 1) {
+                    ws.width >>= 1;
+                    continue;
+                }
+                uint64_t h2 = base + span / 2;
+                while (true) {
+                    c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, &stats[ANN_STAT_WALK_NODES],
+                                 &stats[ANN_STAT_WALK_LEAVES], gk0, gv0, gcap);
+                    stats[ANN_STAT_WALKS]++;
+                    if (c <= gcap) break;
+                    span = h2 - base;
+                    if (span == 0) { cap_err = true; return 0; }
+                    h2 = base + span / 2;
+                }
+                hi = h2;
+            }
+            bool reached_end = (uint32_t)(hi >> 32) >= ws.kmaxall && (uint32_t)hi == 0xffffffffu;
+            ws.lo = hi;
+            ws.first = false;
+            if (reached_end) ws.exhausted = true;
+            if (c == 0) {
+                if (ws.width < 0x40000000u) ws.width <<= 1;
+                continue;
+            }
+            // grow the window while windows stay small
+            if (c < gcap / 16 && ws.width < 0x40000000u) ws.width <<= 2;
+            else if (c < gcap / 4 && ws.width < 0x40000000u) ws.width <<= 1;
+            __syncwarp();
+            ws.gbuf = c > L.bcap ? warp_radix_sort(gk0, gv0, gk1, gv1, c, (uint32_t *)(smem + L.nodes)) : 0;
+            ws.gcnt = c;
+            ws.gpos = 0;
+            break;
+        }
+        if (ws.gcnt == 0) return 0;
+    }
+    // next batch: copy up to bcap entries of the sorted window into shared memory
+    const uint64_t *gk = ws.gbuf ? gk1 : gk0;
+    const uint32_t *gv = ws.gbuf ? gv1 : gv0;
+    const uint32_t c = min(L.bcap, ws.gcnt - ws.gpos);
+    for (uint32_t i = lane; i < c; i += 32) {
+        bkey[i] = gk[ws.gpos + i];
+        bidx[i] = gv[ws.gpos + i];
+    }
+    uint32_t Lp = 1;
+    while (Lp < c) Lp <<= 1;
+    for (uint32_t i = c + lane; i < Lp; i += 32) {
+        bkey[i] = ~0ull;
+        bidx[i] = 0;
+    }
+    __syncwarp();
+    if (ws.gcnt <= L.bcap) warp_sort_pairs(bkey, bidx, (int)Lp);  // small window: sorted here
+    ws.gpos += c;
+    return c;
 }
 
 // Sort part p by (key, center id) in registers; write each center's rank and,
@@ -625,8 +784,8 @@ __device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_
 // ---------------------------------------------------------------------------
 // one query, one warp
 // ---------------------------------------------------------------------------
-template <int DT>
-__device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
+template <int DT, bool WIN>
+__device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8_t *wscratch) {
     const DevIndex &ix = A.ix;
     const WarpLayout &L = A.L;
     const int lane = lane_id();
@@ -708,6 +867,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
 
     // 3. Algorithm 1
     WalkState ws;
+    ws.gpos = ws.gcnt = 0;
+    ws.gbuf = 0;
     ws.lo = 0;
     ws.first = true;
     ws.exhausted = ix.M == 0;
@@ -737,8 +898,9 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
     int32_t pre_row = -1;
 
     while (t < T) {
-        if (bcur >= bcnt && !ws.exhausted) {
-            bcnt = refill<DT>(ix, smem, L, ws, stats, cap_err);
+        if (bcur >= bcnt && (!ws.exhausted || (WIN && ws.gpos < ws.gcnt))) {
+            if (WIN) bcnt = refill_windowed<DT>(ix, smem, L, ws, stats, cap_err, wscratch, A.gcap);
+            else bcnt = refill<DT>(ix, smem, L, ws, stats, cap_err);
             bcur = 0;
             wstart = 0;
             wcnt = 0;
@@ -902,11 +1064,13 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi) {
     __syncwarp();
 }
 
-template <int DT>
+template <int DT, bool WIN>
 __global__ void __launch_bounds__(192, 2) search_kernel(SearchArgs A) {
     extern __shared__ __align__(16) uint8_t smem_all[];
     const int warp = threadIdx.x >> 5;
     uint8_t *smem = smem_all + (size_t)warp * A.L.total;
+    uint8_t *wscratch =
+        WIN ? A.gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * (size_t)A.gcap * 24 : nullptr;
     const int64_t count = A.list_count ? (int64_t)*A.list_count : (A.list ? A.list_len : A.nq);
     if (A.ticket) {
         // persistent: pull queries from the device work queue
@@ -916,14 +1080,14 @@ __global__ void __launch_bounds__(192, 2) search_kernel(SearchArgs A) {
             w = __shfl_sync(0xffffffffu, w, 0);
             if (w >= count) break;
             int64_t qi = A.list ? A.list[w] : w;
-            search_one<DT>(A, smem, qi);
+            search_one<DT, WIN>(A, smem, qi, wscratch);
         }
     } else {
         const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
         const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
         for (int64_t w = gw; w < count; w += nw) {
             int64_t qi = A.list ? A.list[w] : w;
-            search_one<DT>(A, smem, qi);
+            search_one<DT, WIN>(A, smem, qi, wscratch);
         }
     }
 }
@@ -942,6 +1106,12 @@ static int device_props() {
     ANN_CUDA(cudaGetDeviceProperties(&prop, dev));
     g_num_sms = prop.multiProcessorCount;
     g_smem_optin = prop.sharedMemPerBlockOptin;
+    // stream-ordered scratch allocations reuse the pool instead of returning memory at every sync
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     return ANN_OK;
 }
 
@@ -963,7 +1133,7 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     static int regs = 0;
     if (!regs) {
         cudaFuncAttributes fa;
-        regs = cudaFuncGetAttributes(&fa, search_kernel<ANN_U8>) == cudaSuccess ? fa.numRegs : 168;
+        regs = cudaFuncGetAttributes(&fa, search_kernel<ANN_U8, false>) == cudaSuccess ? fa.numRegs : 168;
         if (regs < 32) regs = 32;
     }
     const int warps_by_regs = 65536 / (regs * 32);
@@ -984,9 +1154,30 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     return t;
 }
 
-static int launch_search(const SearchArgs &base, int capT, cudaStream_t stream, bool persistent,
-                         const int32_t *list, const int32_t *list_count, int64_t list_len,
-                         int32_t *ticket) {
+// Budgets from this size on use sorted bridge windows in global scratch: one
+// walk then serves many batches, which pays off when queries pop many bridges.
+static const int kWindowedFromT = 1024;
+
+template <int DT, bool WIN>
+static cudaError_t config_kernel(size_t smem, int threads, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, WIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<DT, WIN>, threads, smem);
+}
+
+// Launch configuration of one search launch: layout, grid and the size of the
+// per-warp global scratch (windowed kernels only).
+struct LaunchCfg {
+    SearchArgs A;
+    dim3 grid, block;
+    size_t smem;
+    bool win;
+    size_t scratch_bytes;
+};
+
+static int plan_launch(const SearchArgs &base, int capT, bool persistent, const int32_t *list,
+                       const int32_t *list_count, int64_t list_len, int32_t *ticket, LaunchCfg &cfg) {
     SearchArgs A = base;
     A.capT = capT;
     Tune tn = choose_tune(A.ix, capT, A.kmax);
@@ -996,36 +1187,63 @@ static int launch_search(const SearchArgs &base, int capT, cudaStream_t stream, 
     A.list_count = list_count;
     A.list_len = list_len;
     A.ticket = ticket;
+    const bool win = capT >= kWindowedFromT;
+    uint32_t gcap = (uint32_t)(2 * capT);
+    if (gcap > 8192) gcap = 8192;
+    A.gcap = win ? gcap : 0;
     size_t smem = (size_t)A.L.total * tn.warps;
     if (smem > g_smem_optin) return fail(ANN_ERR_CAPACITY, "per-query state exceeds shared memory");
     int blocks_per_sm = 0;
-    if (A.ix.dtype == ANN_U8) {
-        ANN_CUDA(cudaFuncSetAttribute(search_kernel<ANN_U8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        ANN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, search_kernel<ANN_U8>,
-                                                               tn.warps * 32, smem));
-    } else {
-        ANN_CUDA(cudaFuncSetAttribute(search_kernel<ANN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
-        ANN_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, search_kernel<ANN_F32>,
-                                                               tn.warps * 32, smem));
-    }
+    const int threads = tn.warps * 32;
+    cudaError_t e;
+    if (A.ix.dtype == ANN_U8)
+        e = win ? config_kernel<ANN_U8, true>(smem, threads, &blocks_per_sm)
+                : config_kernel<ANN_U8, false>(smem, threads, &blocks_per_sm);
+    else
+        e = win ? config_kernel<ANN_F32, true>(smem, threads, &blocks_per_sm)
+                : config_kernel<ANN_F32, false>(smem, threads, &blocks_per_sm);
+    if (e != cudaSuccess) return cuda_fail(e, "search kernel configuration");
     if (blocks_per_sm < 1) blocks_per_sm = 1;
-    int64_t want = list_count ? (int64_t)g_num_sms * blocks_per_sm
-                              : (list_len + tn.warps - 1) / tn.warps;
-    int64_t cap = (int64_t)g_num_sms * blocks_per_sm;
-    if (!persistent && !list_count) {
-        // plain: one warp per query, at most a full wave resident, grid-stride beyond
-        if (want > cap * 4) want = cap * 4;
-    } else {
-        want = cap;
-    }
+    const int64_t cap = (int64_t)g_num_sms * blocks_per_sm;
+    int64_t want = (persistent || list_count) ? cap : (list_len + tn.warps - 1) / tn.warps;
+    // plain launches grid-stride beyond four waves; windowed ones beyond one wave (bounded scratch)
+    const int64_t lim = win ? cap : cap * 4;
+    if (want > lim) want = lim;
     if (want < 1) want = 1;
-    dim3 grid((unsigned)want), block(tn.warps * 32);
-    if (A.ix.dtype == ANN_U8) search_kernel<ANN_U8><<<grid, block, smem, stream>>>(A);
-    else search_kernel<ANN_F32><<<grid, block, smem, stream>>>(A);
+    cfg.A = A;
+    cfg.grid = dim3((unsigned)want);
+    cfg.block = dim3(threads);
+    cfg.smem = smem;
+    cfg.win = win;
+    cfg.scratch_bytes = win ? (size_t)want * tn.warps * gcap * 24 : 0;
+    return ANN_OK;
+}
+
+static int do_launch(LaunchCfg &cfg, uint8_t *scratch, cudaStream_t stream) {
+    cfg.A.gscratch = scratch;
+    if (cfg.A.ix.dtype == ANN_U8) {
+        if (cfg.win) search_kernel<ANN_U8, true><<<cfg.grid, cfg.block, cfg.smem, stream>>>(cfg.A);
+        else search_kernel<ANN_U8, false><<<cfg.grid, cfg.block, cfg.smem, stream>>>(cfg.A);
+    } else {
+        if (cfg.win) search_kernel<ANN_F32, true><<<cfg.grid, cfg.block, cfg.smem, stream>>>(cfg.A);
+        else search_kernel<ANN_F32, false><<<cfg.grid, cfg.block, cfg.smem, stream>>>(cfg.A);
+    }
     ANN_CUDA(cudaGetLastError());
     return ANN_OK;
+}
+
+// plan + stream-ordered scratch (windowed kernels) + launch
+static int launch_search(const SearchArgs &base, int capT, cudaStream_t stream, bool persistent,
+                         const int32_t *list, const int32_t *list_count, int64_t list_len,
+                         int32_t *ticket) {
+    LaunchCfg cfg;
+    int r = plan_launch(base, capT, persistent, list, list_count, list_len, ticket, cfg);
+    if (r != ANN_OK) return r;
+    uint8_t *scratch = nullptr;
+    if (cfg.scratch_bytes) ANN_CUDA(cudaMallocAsync((void **)&scratch, cfg.scratch_bytes, stream));
+    r = do_launch(cfg, scratch, stream);
+    if (scratch) cudaFreeAsync(scratch, stream);
+    return r;
 }
 
 __global__ void max_kernel(const int32_t *v, int64_t n, int32_t *out) {
@@ -1050,7 +1268,8 @@ __global__ void bucket_kernel(int64_t nq, const int32_t *T, int32_t T_all, int32
 
 struct Plan {
     cudaGraphExec_t exec = nullptr;
-    int32_t *scratch = nullptr;  // counts[kBuckets] + tickets[kBuckets] + lists[kBuckets*nq]
+    int32_t *scratch = nullptr;   // counts[kBuckets] + tickets[kBuckets] + lists[kBuckets*nq]
+    uint8_t *wscratch = nullptr;  // per-warp sorted bridge windows (largest windowed bucket's need)
 };
 
 struct PlanKey {
@@ -1081,28 +1300,38 @@ void free_plans(ann_index *ix) {
     for (auto &kv : pc->plans) {
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
         if (kv.second.scratch) cudaFree(kv.second.scratch);
+        if (kv.second.wscratch) cudaFree(kv.second.wscratch);
     }
     delete pc;
     ix->plans = nullptr;
 }
 
+// budgets of the buckets one persistent batch may use
+static void bucket_range(const int32_t *T, int32_t T_all, int &b0, int &b1) {
+    b1 = kBuckets - 1;
+    if (!T) {
+        b1 = 0;
+        while (b1 < kBuckets - 1 && T_all > (128 << b1)) b1++;
+    }
+    b0 = T ? 0 : b1;
+}
+
 static int record_persistent(const SearchArgs &A, int64_t nq, const int32_t *T, int32_t T_all,
-                             int32_t *scratch, cudaStream_t s) {
+                             int32_t *scratch, uint8_t *wscratch, cudaStream_t s) {
     int32_t *counts = scratch, *tickets = scratch + kBuckets, *lists = scratch + 2 * kBuckets;
     ANN_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2 * kBuckets, s));
     if (nq > 0) {
         bucket_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, T, T_all, counts, lists, tickets);
         ANN_CUDA(cudaGetLastError());
     }
-    int maxb = kBuckets - 1;
-    if (!T) {
-        maxb = 0;
-        while (maxb < kBuckets - 1 && T_all > (128 << maxb)) maxb++;
-    }
-    for (int bkt = (T ? 0 : maxb); bkt <= maxb; bkt++) {
+    int b0, b1;
+    bucket_range(T, T_all, b0, b1);
+    for (int bkt = b0; bkt <= b1; bkt++) {
         int capT = 128 << bkt;
         if (capT > kMaxT) capT = kMaxT;
-        int r = launch_search(A, capT, s, true, lists + (int64_t)bkt * nq, counts + bkt, nq, tickets + bkt);
+        LaunchCfg cfg;
+        int r = plan_launch(A, capT, true, lists + (int64_t)bkt * nq, counts + bkt, nq, tickets + bkt, cfg);
+        if (r == ANN_OK) r = do_launch(cfg, wscratch, s);  // buckets run one after another: shared scratch
         if (r != ANN_OK) return r;
     }
     return ANN_OK;
@@ -1189,25 +1418,44 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
     if (it == pc->plans.end()) {
         Plan p;
         ANN_CUDA(cudaMalloc(&p.scratch, sizeof(int32_t) * (2 * kBuckets + (size_t)kBuckets * nq)));
+        {
+            size_t need = 0;
+            int b0, b1;
+            bucket_range(T, T_all, b0, b1);
+            for (int bkt = b0; bkt <= b1; bkt++) {
+                LaunchCfg cfg;
+                int r = plan_launch(A, 128 << bkt, true, nullptr, p.scratch, nq, p.scratch, cfg);
+                if (r != ANN_OK) {
+                    cudaFree(p.scratch);
+                    return r;
+                }
+                need = cfg.scratch_bytes > need ? cfg.scratch_bytes : need;
+            }
+            if (need) {
+                cudaError_t ae = cudaMalloc(&p.wscratch, need);
+                if (ae != cudaSuccess) {
+                    cudaFree(p.scratch);
+                    return cuda_fail(ae, "cudaMalloc(search scratch)");
+                }
+            }
+        }
         cudaStream_t cap;
         ANN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
         ANN_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        int rr = record_persistent(A, nq, T, T_all, p.scratch, cap);
+        int rr = record_persistent(A, nq, T, T_all, p.scratch, p.wscratch, cap);
         cudaError_t ce = cudaStreamEndCapture(cap, &graph);
         cudaStreamDestroy(cap);
-        if (rr != ANN_OK) {
+        if (rr != ANN_OK || ce != cudaSuccess) {
             cudaFree(p.scratch);
-            return rr;
-        }
-        if (ce != cudaSuccess) {
-            cudaFree(p.scratch);
-            return cuda_fail(ce, "cudaStreamEndCapture");
+            if (p.wscratch) cudaFree(p.wscratch);
+            return rr != ANN_OK ? rr : cuda_fail(ce, "cudaStreamEndCapture");
         }
         ce = cudaGraphInstantiate(&p.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) {
             cudaFree(p.scratch);
+            if (p.wscratch) cudaFree(p.wscratch);
             return cuda_fail(ce, "cudaGraphInstantiate");
         }
         it = pc->plans.emplace(key, p).first;
