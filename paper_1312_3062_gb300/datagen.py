@@ -126,6 +126,20 @@ def per_query_params(workload: int, nq: int, seed_salt: int = 20):
     return k, T
 
 
+def mixture(seed: int, N: int, d: int, ncomp: int, dtype) -> np.ndarray:
+    """Small seeded mixtures for parity cases: uint8 rows as in workload 1
+    (means U[0,255], sigma 20, rint + clip), float32 rows as in workload 3
+    (means U[0,1], sigma 0.15, folded at 0, L2-normalised)."""
+    rng = np.random.default_rng(seed)
+    if dtype == np.uint8:
+        means = rng.uniform(0, 255, size=(ncomp, d))
+        x = means[rng.integers(0, ncomp, N)] + rng.standard_normal((N, d)) * 20.0
+        return np.clip(np.rint(x), 0, 255).astype(np.uint8)
+    means = rng.uniform(0, 1, size=(ncomp, d))
+    x = np.abs(means[rng.integers(0, ncomp, N)] + rng.standard_normal((N, d)) * 0.15)
+    return (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
+
+
 def poisson_requests(workload: int, nreq: int, rate_qps: float, seed_salt: int = 30):
     """Poisson arrivals of request batches: (arrival_s, batch_size) arrays;
     batch sizes log-uniform integers in [1, 512]."""

@@ -34,15 +34,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-def gmm(seed, N, d, ncomp, dtype):
-    rng = np.random.default_rng(seed)
-    if dtype == np.uint8:
-        means = rng.uniform(0, 255, size=(ncomp, d))
-        x = means[rng.integers(0, ncomp, N)] + rng.standard_normal((N, d)) * 20.0
-        return np.clip(np.rint(x), 0, 255).astype(np.uint8)
-    means = rng.uniform(0, 1, size=(ncomp, d))
-    x = np.abs(means[rng.integers(0, ncomp, N)] + rng.standard_normal((N, d)) * 0.15)
-    return (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
+gmm = datagen.mixture
 
 
 def gpu_keys(t, dtype):
