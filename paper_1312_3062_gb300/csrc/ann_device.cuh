@@ -73,8 +73,8 @@ __device__ inline void warp_sort_pairs(uint64_t *keys, uint32_t *vals, int L) {
 // Bitonic sort of 32*EPL keys held in registers, ascending in the blocked
 // order (element i = lane*EPL + slot).  Pairs in different lanes exchange
 // through shuffles; pairs in the same lane swap registers.
-template <int EPL>
-__device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
+template <int EPL, typename K>
+__device__ __forceinline__ void reg_bitonic_sort_t(K (&v)[EPL]) {
     const int lane = lane_id();
     constexpr int L = 32 * EPL;
 #pragma unroll
@@ -85,9 +85,9 @@ __device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
 #pragma unroll
                 for (int s = 0; s < EPL; s++) {
                     const int i = lane * EPL + s;
-                    const uint64_t o = __shfl_xor_sync(0xffffffffu, v[s], j / EPL);
+                    const K o = __shfl_xor_sync(0xffffffffu, v[s], j / EPL);
                     const bool up = (i & k) == 0, lower = (i & j) == 0;
-                    const uint64_t mn = v[s] < o ? v[s] : o, mx = v[s] < o ? o : v[s];
+                    const K mn = v[s] < o ? v[s] : o, mx = v[s] < o ? o : v[s];
                     v[s] = (lower == up) ? mn : mx;
                 }
             } else {
@@ -96,7 +96,7 @@ __device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
                     const int p = s ^ j;
                     if (p > s) {
                         const bool up = ((lane * EPL + s) & k) == 0;
-                        const uint64_t a = v[s], b = v[p];
+                        const K a = v[s], b = v[p];
                         if ((a > b) == up) {
                             v[s] = b;
                             v[p] = a;
@@ -106,6 +106,11 @@ __device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
             }
         }
     }
+}
+
+template <int EPL>
+__device__ __forceinline__ void reg_bitonic_sort(uint64_t (&v)[EPL]) {
+    reg_bitonic_sort_t<EPL, uint64_t>(v);
 }
 
 // ---------------------------------------------------------------------------

@@ -26,6 +26,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "ann_device.cuh"
@@ -37,14 +38,19 @@ namespace ann {
 // shared-memory layout of one warp
 // ---------------------------------------------------------------------------
 struct WarpLayout {
-    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, misc, total;
-    uint32_t heap_cap, hash_log, bcap, ncap;
+    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, stage, sid,
+        misc, total;
+    uint32_t heap_cap, hash_log, bcap, ncap, stage_rows;
 };
+
+// Rows of the next pop's neighbours staged in shared memory: on when a whole
+// adjacency list of vectors fits in this many bytes.
+constexpr uint32_t kStageBytes = 4096;
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
-                                                  int kmax, int bcap, int b) {
+                                                  int kmax, int bcap, int b, int R) {
     WarpLayout L;
     uint32_t o = 0;
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
@@ -65,21 +71,30 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.bcap = (uint32_t)bcap;
     L.bkey = o;   o = align_up(o + 8u * bcap, 16);
     L.bidx = o;   o = align_up(o + 4u * bcap, 16);
-    // scratch shared by the walk (prefix sums + node list) and the main loop
-    // (candidate ids + keys); the two never overlap in time
+    // candidate ids + keys of the main loop
     const uint32_t wb = 32u * (uint32_t)b;  // bridge-window entries
-    L.ncap = 64;
-    uint32_t walk_bytes = align_up(4u * (n + 1), 16) + 16u * L.ncap;
     uint32_t cand_n = wb > 32u ? wb : 32u;
-    uint32_t main_bytes = align_up(4u * cand_n, 16) * 2;
+    L.cand = o;   o = align_up(o + 4u * cand_n, 16);
+    L.ckey = o;   o = align_up(o + 4u * cand_n, 16);
+    // one region shared by three users that are never live at the same time:
+    // the walk (prefix sums + node list), the bridge window (reference ids +
+    // keys) and the staged neighbour vectors of the next pop
+    const uint32_t vb = (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u);
+    L.stage_rows = (uint32_t)R * vb <= kStageBytes ? (uint32_t)R : 0u;
+    L.ncap = 64;
+    const uint32_t walk_bytes = align_up(4u * (n + 1), 16) + 16u * L.ncap;
+    const uint32_t win_bytes = 2u * align_up(4u * wb, 16);
+    const uint32_t stage_bytes = L.stage_rows * vb;
+    uint32_t ub = walk_bytes > win_bytes ? walk_bytes : win_bytes;
+    if (stage_bytes > ub) ub = stage_bytes;
     L.pref = o;
     L.nodes = o + align_up(4u * (n + 1), 16);
-    L.cand = o;
-    L.ckey = o + align_up(4u * cand_n, 16);
-    o = align_up(o + (walk_bytes > main_bytes ? walk_bytes : main_bytes), 16);
-    L.wref = o;   o = align_up(o + 4u * wb, 16);
-    L.wkey = o;   o = align_up(o + 4u * wb, 16);
-    L.misc = o;   o = align_up(o + 16u * 4, 16);
+    L.wref = o;
+    L.wkey = o + align_up(4u * wb, 16);
+    L.stage = o;
+    o = align_up(o + ub, 16);
+    L.sid = o;    o = align_up(o + 4u * (uint32_t)R, 16);
+    L.misc = o;   o = align_up(o + 16u * 4, 16);  // [0] emit count, [3] min suffix, [8..10] walk counters
     L.total = o;
     return L;
 }
@@ -346,8 +361,60 @@ __device__ void cand_distances(const DevIndex &ix, const uint8_t *qbytes, const 
     __syncwarp();
 }
 
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+// 16-byte asynchronous global -> shared copies (L2 only), completed per thread
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// distances of m rows already staged in shared memory (row j at stage + j*vb)
+template <int DT>
+__device__ void stage_distances(const uint8_t *stage, const uint8_t *qbytes, int vb, int m, uint32_t *ckey) {
+    const int lane = lane_id();
+    const int nc = vb >> 4;
+    int G = 1;
+    while (G * 2 <= nc && G * 2 <= 32) G *= 2;
+    const int per_round = 32 / G;
+    const int lig = lane & (G - 1);
+    const int grp = lane / G;
+    const uint4 *qv = (const uint4 *)qbytes;
+    for (int base = 0; base < m; base += per_round) {
+        const int j = base + grp;
+        uint32_t acc = 0;
+        float hi = 0.f, lo = 0.f;
+        if (j < m) {
+            const uint4 *row = (const uint4 *)(stage + (size_t)j * vb);
+            for (int c = lig; c < nc; c += G) {
+                const uint4 a = row[c], q = qv[c];
+                if (DT == ANN_U8) {
+                    uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
+                    uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
+                    acc = __dp4a(d0, d0, acc);
+                    acc = __dp4a(d1, d1, acc);
+                    acc = __dp4a(d2, d2, acc);
+                    acc = __dp4a(d3, d3, acc);
+                } else {
+                    df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
+                    df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
+                }
+            }
+        }
+        for (int off = G >> 1; off > 0; off >>= 1) {
+            if (DT == ANN_U8) {
+                acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            } else {
+                float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
+                float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
+                df_add(hi, lo, h2, l2);
+            }
+        }
+        if (j < m && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
+    }
+    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -371,7 +438,7 @@ struct WalkState {
 // are processed as one flat range, 32 consecutive leaves per step.
 template <int DT>
 __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
-                         uint64_t hi, int64_t *st_nodes, int64_t *st_leaves, uint64_t *okey, uint32_t *oval,
+                         uint64_t hi, uint64_t *okey, uint32_t *oval,
                          uint32_t ocap) {
     const int lane = lane_id();
     const int n = ix.n, P = ix.P, PA = ix.PA;
@@ -528,8 +595,9 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     __syncwarp();
     for (int off = 16; off > 0; off >>= 1) nodes_here += __shfl_xor_sync(0xffffffffu, nodes_here, off);
     if (lane == 0) {
-        *st_nodes += nodes_here;
-        *st_leaves += leaves_here;
+        cnt[8]++;
+        cnt[9] += (uint32_t)nodes_here;
+        cnt[10] += (uint32_t)leaves_here;
     }
     __syncwarp();
     return cnt[0];
@@ -547,15 +615,13 @@ __device__ __forceinline__ uint64_t window_end(uint64_t lo, bool first, uint32_t
 // Refill the batch: bridges after ws.lo in order.  Returns count (0 = none left).
 template <int DT>
 __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, WalkState &ws,
-                           int64_t *stats, bool &cap_err) {
+                           bool &cap_err) {
     uint64_t *bkey = (uint64_t *)(smem + L.bkey);
     uint32_t *bidx = (uint32_t *)(smem + L.bidx);
     const int lane = lane_id();
     while (!ws.exhausted) {
         uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
-        uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, &stats[ANN_STAT_WALK_NODES],
-                              &stats[ANN_STAT_WALK_LEAVES], bkey, bidx, L.bcap);
-        stats[ANN_STAT_WALKS]++;
+        uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, bkey, bidx, L.bcap);
         if (c > L.bcap) {
             // too many in the window: halve it (in composite space)
             uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
@@ -569,10 +635,8 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
             // width 1 key unit: split the composite range directly
             uint64_t h2 = base + span / 2;
             while (true) {
-                c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, &stats[ANN_STAT_WALK_NODES],
-                             &stats[ANN_STAT_WALK_LEAVES], bkey, bidx, L.bcap);
-                stats[ANN_STAT_WALKS]++;
-                if (c <= L.bcap) break;
+                c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, bkey, bidx, L.bcap);
+                        if (c <= L.bcap) break;
                 span = h2 - base;
                 if (span == 0) { cap_err = true; return 0; }
                 h2 = base + span / 2;
@@ -676,7 +740,7 @@ __device__ int warp_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_
 // from it bcap entries at a time.  Returns the count (0 = none left).
 template <int DT>
 __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, WalkState &ws,
-                           int64_t *stats, bool &cap_err, uint8_t *wscratch, uint32_t gcap) {
+                                    bool &cap_err, uint8_t *wscratch, uint32_t gcap) {
     uint64_t *gk0 = (uint64_t *)wscratch;
     uint64_t *gk1 = gk0 + gcap;
     uint32_t *gv0 = (uint32_t *)(gk1 + gcap);
@@ -688,10 +752,8 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
         ws.gpos = ws.gcnt = 0;
         while (!ws.exhausted) {
             uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
-            uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, &stats[ANN_STAT_WALK_NODES],
-                                  &stats[ANN_STAT_WALK_LEAVES], gk0, gv0, gcap);
-            stats[ANN_STAT_WALKS]++;
-            if (c > gcap) {
+            uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, gk0, gv0, gcap);
+                if (c > gcap) {
                 // too many in the window: halve it (in composite space)
                 uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
                 uint64_t span = hi - base;
@@ -702,10 +764,8 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
                 }
                 uint64_t h2 = base + span / 2;
                 while (true) {
-                    c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, &stats[ANN_STAT_WALK_NODES],
-                                 &stats[ANN_STAT_WALK_LEAVES], gk0, gv0, gcap);
-                    stats[ANN_STAT_WALKS]++;
-                    if (c <= gcap) break;
+                    c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, gk0, gv0, gcap);
+                                if (c <= gcap) break;
                     span = h2 - base;
                     if (span == 0) { cap_err = true; return 0; }
                     h2 = base + span / 2;
@@ -753,32 +813,56 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
 
 // Sort part p by (key, center id) in registers; write each center's rank and,
 // for prefix parts, the center id at each rank; record the first/last key.
-template <int EPL>
+// PACK: uint8 part keys below 2^24 travel as one 32-bit word (key << 8 | id),
+// which orders exactly like the (key, id) pair.
+template <int EPL, bool PACK>
 __device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_t *sc, int p, int n, int PA,
                                           uint32_t *first_keys, uint32_t *last_keys) {
     const int lane = lane_id();
-    uint64_t v[EPL];
+    using K = typename std::conditional<PACK, uint32_t, uint64_t>::type;
+    constexpr int SH = PACK ? 8 : 32;
+    K v[EPL];
 #pragma unroll
     for (int s = 0; s < EPL; s++) {
         const int c = lane * EPL + s;
-        v[s] = c < n ? (((uint64_t)D[p * n + c]) << 32) | (uint32_t)c : ~0ull;
+        v[s] = c < n ? (((K)D[p * n + c]) << SH) | (K)c : ~(K)0;
     }
-    reg_bitonic_sort<EPL>(v);
+    reg_bitonic_sort_t<EPL, K>(v);
 #pragma unroll
     for (int s = 0; s < EPL; s++) {
         const int r = lane * EPL + s;
         if (r < n) {
-            const uint32_t c = (uint32_t)v[s];
+            const uint32_t c = (uint32_t)(v[s] & (PACK ? 0xffu : 0xffffffffu));
             rk[p * n + c] = (uint8_t)r;
             if (p < PA) sc[p * n + r] = (uint8_t)c;
         }
     }
-    first_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> 32);
-    uint64_t lastv = v[0];
+    first_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> SH);
+    K lastv = v[0];
 #pragma unroll
     for (int s = 0; s < EPL; s++)
         if (s == (n - 1) % EPL) lastv = v[s];
-    last_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, lastv, (n - 1) / EPL) >> 32);
+    last_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, lastv, (n - 1) / EPL) >> SH);
+}
+
+template <int DT>
+__device__ __forceinline__ void sort_parts(const uint32_t *D, uint8_t *rk, uint8_t *sc, int P, int n, int PA,
+                                           int dp, uint32_t *first_keys, uint32_t *last_keys) {
+    // uint8 part keys are at most dp * 255^2
+    const bool pack = DT == ANN_U8 && (uint64_t)dp * 65025u < (1u << 24);
+    for (int p = 0; p < P; p++) {
+        if (pack) {
+            if (n <= 32) sort_part<1, true>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 64) sort_part<2, true>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 128) sort_part<4, true>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else sort_part<8, true>(D, rk, sc, p, n, PA, first_keys, last_keys);
+        } else {
+            if (n <= 32) sort_part<1, false>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 64) sort_part<2, false>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else if (n <= 128) sort_part<4, false>(D, rk, sc, p, n, PA, first_keys, last_keys);
+            else sort_part<8, false>(D, rk, sc, p, n, PA, first_keys, last_keys);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -793,8 +877,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     const int k = A.k ? A.k[qi] : A.k_all;
     const int T = A.T ? A.T[qi] : A.T_all;
     int32_t *oid = A.out_ids + qi * A.kmax;
-    int64_t stats[ANN_NSTATS];
-    for (int i = 0; i < ANN_NSTATS; i++) stats[i] = 0;
+    // per-query counters (registers; the walk keeps its own in shared memory)
+    uint32_t n_refpops = 0, n_brpops = 0, n_ready = 0;
     if (k < 0 || k > A.kmax || T < 0 || T > A.capT) {
         for (int j = lane; j < A.kmax; j += 32) {
             oid[j] = -1;
@@ -823,8 +907,9 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         uint4 *dst = (uint4 *)qb;
         for (int c = lane; c < (vb >> 4); c += 32) dst[c] = __ldg(src + c);
     }
-    // clear the visited set
+    // clear the visited set and the walk counters
     for (uint32_t i = lane; i < (1u << L.hash_log); i += 32) H[i] = 0;
+    if (lane < 16) misc[lane] = 0;
     __syncwarp();
 
     // 1. part tables
@@ -838,12 +923,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     uint32_t kmin = 0, kmaxall = 0;
     {
         uint32_t first_keys[kMaxP], last_keys[kMaxP];
-        for (int p = 0; p < P; p++) {
-            if (n <= 32) sort_part<1>(D, rk, sc, p, n, PA, first_keys, last_keys);
-            else if (n <= 64) sort_part<2>(D, rk, sc, p, n, PA, first_keys, last_keys);
-            else if (n <= 128) sort_part<4>(D, rk, sc, p, n, PA, first_keys, last_keys);
-            else sort_part<8>(D, rk, sc, p, n, PA, first_keys, last_keys);
-        }
+        sort_parts<DT>(D, rk, sc, P, n, PA, dp, first_keys, last_keys);
         __syncwarp();
         // smallest / largest bridge keys and the min-suffix sum, grouped (D0+D1)+(D2+...)
         auto group_sum = [&](const uint32_t *v) -> uint32_t {
@@ -894,13 +974,38 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     const int b = ix.b, R = ix.R;
     int32_t *wref = (int32_t *)(smem + L.wref);
     uint32_t *wkey = (uint32_t *)(smem + L.wkey);
-    uint32_t pre_id = 0xffffffffu;  // reference whose kNN row is already in `pre_row`
-    int32_t pre_row = -1;
+    // The next pop, once known, is staged: its kNN row in registers (nx_row)
+    // and, when stage_rows > 0, its unvisited neighbours' vectors copied into
+    // shared memory by cp.async (nx_vec, nx_mask = which row entries are new,
+    // cut to the budget).  The vectors and mask stay valid only while nothing
+    // else is discovered, i.e. for the very next step.  Right after every
+    // reference pop the new heap root's row is loaded speculatively (sp_row):
+    // it is the next pop unless the expansion finds a smaller key.
+    constexpr uint32_t kNone = 0xffffffffu;
+    uint32_t nx_id = kNone, sp_id = kNone;
+    int32_t nx_row = -1, sp_row = -1;
+    bool nx_vec = false, cp_out = false;
+    unsigned nx_mask = 0;
+    const int vbytes = ix.d * (DT == ANN_U8 ? 1 : 4);
+    // staged rows are handled by groups of sG lanes (16-byte chunks of a row)
+    const int snc = vbytes >> 4;
+    int sG = 1;
+    while (sG * 2 <= snc && sG * 2 <= 32) sG *= 2;
+    const int sper = 32 / sG, slig = lane & (sG - 1), sgrp = lane / sG;
+    uint8_t *stage = smem + L.stage;
+    int32_t *sid = (int32_t *)(smem + L.sid);
 
     while (t < T) {
         if (bcur >= bcnt && (!ws.exhausted || (WIN && ws.gpos < ws.gcnt))) {
-            if (WIN) bcnt = refill_windowed<DT>(ix, smem, L, ws, stats, cap_err, wscratch, A.gcap);
-            else bcnt = refill<DT>(ix, smem, L, ws, stats, cap_err);
+            // the walk reuses the staging region
+            if (cp_out) {
+                cp_async_wait_all();
+                cp_out = false;
+            }
+            nx_vec = false;
+            __syncwarp();
+            if (WIN) bcnt = refill_windowed<DT>(ix, smem, L, ws, cap_err, wscratch, A.gcap);
+            else bcnt = refill<DT>(ix, smem, L, ws, cap_err);
             bcur = 0;
             wstart = 0;
             wcnt = 0;
@@ -915,20 +1020,39 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         int32_t x = -1;
         uint32_t xkey = 0;
         bool have_key = false;
+        bool staged = false;
         int alen;
         if (take_ref) {
             uint32_t p = (uint32_t)top;
             heap_pop(heap, hsz);
             alen = R;
-            if (p == pre_id) {
-                x = pre_row;
-                stats[ANN_STAT_PRELOADED]++;
+            if (p == nx_id) {
+                x = nx_row;
+                staged = nx_vec;
+                n_ready++;
+            } else if (p == sp_id) {
+                x = sp_row;
+                n_ready++;
             } else if (lane < R) {
                 x = __ldg(ix.G + (int64_t)p * R + lane);
             }
-            pre_id = 0xffffffffu;
-            stats[ANN_STAT_REF_POPS]++;
+            nx_id = kNone;
+            nx_vec = false;
+            if (hsz > 0) {
+                sp_id = (uint32_t)heap[0];
+                sp_row = lane < R ? __ldg(ix.G + (int64_t)sp_id * R + lane) : -1;
+            } else {
+                sp_id = kNone;
+            }
+            n_refpops++;
         } else {
+            // the bridge window reuses the staging region
+            if (cp_out) {
+                cp_async_wait_all();
+                cp_out = false;
+            }
+            nx_vec = false;
+            __syncwarp();
             if (bcur >= wstart + wcnt) {
                 // fill the window: reference lists of the next bridges and their distances
                 wstart = bcur;
@@ -967,35 +1091,81 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                 xkey = wkey[wi + lane];
             }
             have_key = true;
-            stats[ANN_STAT_BRIDGE_POPS]++;
+            n_brpops++;
         }
-        bool isnew = lane < alen && x >= 0 && x < ix.N && !hash_has(H, L.hash_log, (uint32_t)x);
-        unsigned mask = __ballot_sync(0xffffffffu, isnew);
-        int room = T - t;
-        while (__popc(mask) > room) mask &= ~(1u << (31 - __clz(mask)));  // keep the first `room` in list order
-        int m = __popc(mask);
-        if (m == 0) continue;
-        if ((mask >> lane) & 1u) {
-            int pos = __popc(mask & ((1u << lane) - 1));
-            cand[pos] = (uint32_t)x;
-            if (have_key) ckey[pos] = xkey;
-            hash_add(H, L.hash_log, (uint32_t)x);
+        unsigned mask;
+        if (staged) {
+            mask = nx_mask;  // computed one step earlier against the same visited set and budget
+        } else {
+            bool isnew = lane < alen && x >= 0 && x < ix.N && !hash_has(H, L.hash_log, (uint32_t)x);
+            mask = __ballot_sync(0xffffffffu, isnew);
+            int room = T - t;
+            while (__popc(mask) > room) mask &= ~(1u << (31 - __clz(mask)));  // keep the first `room` in list order
         }
-        __syncwarp();
-        if (!have_key) cand_distances<DT>(ix, qb, cand, m, ckey);
-        uint64_t mine = lane < m ? (((uint64_t)ckey[lane] << 32) | cand[lane]) : ~0ull;
-        heap_push_batch(heap, hsz, mine, m);
-        if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
-        // The next pop is known now: when it is a reference, start loading its
-        // kNN row so that the load overlaps the result-set update below.
+        const int m = __popc(mask);
+        uint64_t mine = ~0ull;
+        if (m > 0) {
+            if ((mask >> lane) & 1u) {
+                int pos = __popc(mask & ((1u << lane) - 1));
+                cand[pos] = (uint32_t)x;
+                if (have_key) ckey[pos] = xkey;
+                hash_add(H, L.hash_log, (uint32_t)x);
+            }
+            __syncwarp();
+            if (!have_key) {
+                if (staged) {
+                    cp_async_wait_all();
+                    cp_out = false;
+                    __syncwarp();
+                    stage_distances<DT>(stage, qb, vbytes, m, ckey);
+                } else {
+                    cand_distances<DT>(ix, qb, cand, m, ckey);
+                }
+            }
+            mine = lane < m ? (((uint64_t)ckey[lane] << 32) | cand[lane]) : ~0ull;
+            heap_push_batch(heap, hsz, mine, m);
+            if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
+        }
+        // The next pop is known now.  When it is a reference, take its kNN row
+        // (usually the speculative one) and start copying its unvisited
+        // neighbours' vectors, so both overlap the rest of this step and the
+        // next pop.
         if (t + m < T && hsz > 0) {
-            uint64_t ntop = heap[0];
-            bool next_ref = bcur >= bcnt ? (ws.exhausted || true) : (uint32_t)(ntop >> 32) <= (uint32_t)(bkey[bcur] >> 32);
-            if (next_ref) {
-                pre_id = (uint32_t)ntop;
-                pre_row = lane < R ? __ldg(ix.G + (int64_t)pre_id * R + lane) : -1;
+            const uint64_t ntop = heap[0];
+            const bool maybe_ref = bcur >= bcnt || (uint32_t)(ntop >> 32) <= (uint32_t)(bkey[bcur] >> 32);
+            if (maybe_ref) {
+                const uint32_t nid = (uint32_t)ntop;
+                if (nid != nx_id) {
+                    nx_row = nid == sp_id ? sp_row : (lane < R ? __ldg(ix.G + (int64_t)nid * R + lane) : -1);
+                    nx_id = nid;
+                }
+                // vectors only when the next step is certainly this pop (no
+                // refill first) and no bridge-window entries are still pending
+                const bool refill_next = bcur >= bcnt && (!ws.exhausted || (WIN && ws.gpos < ws.gcnt));
+                if (L.stage_rows && !refill_next && bcur >= wstart + wcnt) {
+                    const bool nw = lane < R && nx_row >= 0 && nx_row < ix.N &&
+                                    !hash_has(H, L.hash_log, (uint32_t)nx_row);
+                    unsigned mk = __ballot_sync(0xffffffffu, nw);
+                    const int room2 = T - (t + m);
+                    while (__popc(mk) > room2) mk &= ~(1u << (31 - __clz(mk)));
+                    nx_mask = mk;
+                    nx_vec = true;
+                    if (mk) {
+                        if ((mk >> lane) & 1u) sid[__popc(mk & ((1u << lane) - 1))] = nx_row;
+                        __syncwarp();
+                        const int m2 = __popc(mk);
+                        for (int j = sgrp; j < m2; j += sper) {
+                            const uint8_t *src = (const uint8_t *)ix.X + (int64_t)sid[j] * vbytes;
+                            uint8_t *dst = stage + (size_t)j * vbytes;
+                            for (int c = slig; c < snc; c += sG) cp_async16(dst + 16 * c, src + 16 * c);
+                        }
+                        cp_async_commit();
+                        cp_out = true;
+                    }
+                }
             }
         }
+        if (m == 0) continue;
         // result set: the k smallest by (key, id)
         if (rsmall) {
             if (k > 0) {
@@ -1040,12 +1210,13 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         }
         t += m;
     }
+    // nothing may still land in shared memory once this query ends
+    if (cp_out) cp_async_wait_all();
+    __syncwarp();
     if (rsmall) {
         if (lane < k) rbuf[lane] = rreg;
         __syncwarp();
     }
-    stats[ANN_STAT_DISCOVERED] = t;
-    stats[ANN_STAT_MAX_Q] = maxq;
     __syncwarp();
     // outputs
     for (int j = lane; j < A.kmax; j += 32) {
@@ -1058,8 +1229,17 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     }
     if (lane == 0) {
         if (A.out_status) A.out_status[qi] = cap_err ? ANN_ERR_CAPACITY : ANN_OK;
-        if (A.out_stats)
-            for (int i = 0; i < ANN_NSTATS; i++) A.out_stats[qi * ANN_NSTATS + i] = stats[i];
+        if (A.out_stats) {
+            int64_t *o = A.out_stats + qi * ANN_NSTATS;
+            o[ANN_STAT_DISCOVERED] = t;
+            o[ANN_STAT_REF_POPS] = n_refpops;
+            o[ANN_STAT_BRIDGE_POPS] = n_brpops;
+            o[ANN_STAT_WALKS] = misc[8];
+            o[ANN_STAT_WALK_NODES] = misc[9];
+            o[ANN_STAT_WALK_LEAVES] = misc[10];
+            o[ANN_STAT_MAX_Q] = maxq;
+            o[ANN_STAT_PRELOADED] = n_ready;
+        }
     }
     __syncwarp();
 }
@@ -1115,6 +1295,10 @@ static int device_props() {
     return ANN_OK;
 }
 
+// Budgets from this size on use sorted bridge windows in global scratch: one
+// walk then serves many batches, which pays off when queries pop many bridges.
+static const int kWindowedFromT = 1024;
+
 // Launch configuration for a budget bucket: warps per CTA and batch capacity.
 struct Tune {
     int warps;
@@ -1125,8 +1309,9 @@ struct Tune {
 // the per-warp shared-memory slice (ties go to more warps per CTA).
 static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     Tune t;
-    t.bcap = 128;
-    WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b);
+    // bridge batch: budgets below the windowed kernels pop few bridges
+    t.bcap = capT >= kWindowedFromT ? 128 : 64;
+    WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b, ix.R);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
     // register-file limit of the kernel (both instantiations use the same budget)
@@ -1154,9 +1339,6 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     return t;
 }
 
-// Budgets from this size on use sorted bridge windows in global scratch: one
-// walk then serves many batches, which pays off when queries pop many bridges.
-static const int kWindowedFromT = 1024;
 
 template <int DT, bool WIN>
 static cudaError_t config_kernel(size_t smem, int threads, int *blocks_per_sm) {
@@ -1182,7 +1364,7 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     A.capT = capT;
     Tune tn = choose_tune(A.ix, capT, A.kmax);
     A.bcap = tn.bcap;
-    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b);
+    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b, A.ix.R);
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
