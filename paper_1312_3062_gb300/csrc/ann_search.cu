@@ -38,9 +38,9 @@ namespace ann {
 // shared-memory layout of one warp
 // ---------------------------------------------------------------------------
 struct WarpLayout {
-    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, stage, sid,
-        misc, total;
-    uint32_t heap_cap, hash_log, bcap, ncap, stage_rows;
+    uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, stage, misc,
+        total;
+    uint32_t heap_cap, hash_log, bcap, ncap, stage_rows, stage_stride;
 };
 
 // Rows of the next pop's neighbours staged in shared memory: on when a whole
@@ -84,7 +84,10 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.ncap = 64;
     const uint32_t walk_bytes = align_up(4u * (n + 1), 16) + 16u * L.ncap;
     const uint32_t win_bytes = 2u * align_up(4u * wb, 16);
-    const uint32_t stage_bytes = L.stage_rows * vb;
+    // staged rows are padded by 16 bytes so that lanes reading different rows
+    // at the same offset fall into different banks
+    L.stage_stride = vb + 16;
+    const uint32_t stage_bytes = L.stage_rows * L.stage_stride;
     uint32_t ub = walk_bytes > win_bytes ? walk_bytes : win_bytes;
     if (stage_bytes > ub) ub = stage_bytes;
     L.pref = o;
@@ -93,7 +96,6 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.wkey = o + align_up(4u * wb, 16);
     L.stage = o;
     o = align_up(o + ub, 16);
-    L.sid = o;    o = align_up(o + 4u * (uint32_t)R, 16);
     L.misc = o;   o = align_up(o + 16u * 4, 16);  // [0] emit count, [3] min suffix, [8..10] walk counters
     L.total = o;
     return L;
@@ -141,6 +143,21 @@ __device__ __forceinline__ bool hash_has(const uint32_t *H, uint32_t log, uint32
     }
     return false;
 }
+// membership test that also reports where the probe ended: the slot holding
+// x, or the empty slot an insertion of x would take (~0 if the table is full)
+__device__ __forceinline__ bool hash_find(const uint32_t *H, uint32_t log, uint32_t x, uint32_t &slot) {
+    uint32_t mask = (1u << log) - 1, h = hslot(x, log);
+    for (uint32_t i = 0; i <= mask; i++) {
+        uint32_t v = H[h];
+        if (v == x + 1 || v == 0) {
+            slot = h;
+            return v != 0;
+        }
+        h = (h + 1) & mask;
+    }
+    slot = 0xffffffffu;
+    return false;
+}
 __device__ __forceinline__ void hash_add(uint32_t *H, uint32_t log, uint32_t x) {
     uint32_t mask = (1u << log) - 1, h = hslot(x, log);
     for (uint32_t i = 0; i <= mask; i++) {
@@ -166,41 +183,10 @@ __device__ __forceinline__ void warp_argmin(uint64_t &v, uint32_t &i) {
     v = ((uint64_t)mh << 32) | ml;
 }
 
-// append m entries (lane j holds entry j, j < m) and restore the heap order:
-// every new entry checks its parent in parallel; only those smaller than
-// their parent sift up, one after another (values on a sift-up path only
-// decrease, so entries that passed the check stay valid)
-__device__ __forceinline__ void heap_push_batch(uint64_t *h, uint32_t &sz, uint64_t e, int m) {
-    const int lane = lane_id();
-    const uint32_t pos = sz + lane;
-    if (lane < m) h[pos] = e;
-    __syncwarp();
-    bool need = lane < m && pos > 0 && h[(pos - 1) >> 5] > e;
-    unsigned nm = __ballot_sync(0xffffffffu, need);
-    if (nm) {
-        __syncwarp();
-        if (lane == 0) {
-            while (nm) {
-                int j = __ffs(nm) - 1;
-                nm &= nm - 1;
-                uint32_t i = sz + j;
-                uint64_t v = h[i];
-                while (i > 0) {
-                    uint32_t p = (i - 1) >> 5;
-                    uint64_t pv = h[p];
-                    if (pv <= v) break;
-                    h[i] = pv;
-                    i = p;
-                }
-                h[i] = v;
-            }
-        }
-    }
-    sz += m;
-    __syncwarp();
-}
-
-// remove the minimum (the caller has read h[0]); all lanes take part
+// remove the minimum (the caller has read h[0]); all lanes take part.  Per
+// level: the smallest child key by one warp reduction; only when several
+// children share it a second reduction over their ids.  The lane holding the
+// smallest child moves it up.
 __device__ __forceinline__ void heap_pop(uint64_t *h, uint32_t &sz) {
     const int lane = lane_id();
     sz--;
@@ -208,18 +194,59 @@ __device__ __forceinline__ void heap_pop(uint64_t *h, uint32_t &sz) {
     uint32_t i = 0;
     __syncwarp();
     for (;;) {
-        uint32_t c0 = 32 * i + 1;
+        const uint32_t c0 = 32 * i + 1;
         if (c0 >= sz) break;
-        uint32_t ci = c0 + lane;
-        uint64_t cv = ci < sz ? h[ci] : ~0ull;
-        warp_argmin(cv, ci);
-        if (cv >= v) break;
-        __syncwarp();
-        if (lane == 0) h[i] = cv;
-        i = ci;
+        const uint32_t ci = c0 + lane;
+        const uint64_t cv = ci < sz ? h[ci] : ~0ull;
+        const uint32_t hi = (uint32_t)(cv >> 32);
+        const uint32_t mh = __reduce_min_sync(0xffffffffu, hi);
+        unsigned who = __ballot_sync(0xffffffffu, hi == mh);
+        if (who & (who - 1)) {
+            const uint32_t ml = __reduce_min_sync(0xffffffffu, hi == mh ? (uint32_t)cv : 0xffffffffu);
+            who = __ballot_sync(0xffffffffu, hi == mh && (uint32_t)cv == ml);
+        }
+        const int w = __ffs(who) - 1;
+        if (__ballot_sync(0xffffffffu, lane == w && cv >= v)) break;
+        if (lane == w) h[i] = cv;
+        i = c0 + (uint32_t)w;
     }
     __syncwarp();
     if (lane == 0 && sz > 0) h[i] = v;
+    __syncwarp();
+}
+
+// append the entries of the lanes in `mask` (lane l holds entry e, stored at
+// sz + pos, pos = its rank in the mask) and restore the heap order: every
+// new entry checks its parent in parallel; those smaller than their parent
+// sift up one after another (the new entries are leaves, or children of a
+// new root, so any order of the sift-ups gives a valid heap)
+__device__ __forceinline__ void heap_push_masked(uint64_t *h, uint32_t &sz, uint64_t e, unsigned mask, int pos) {
+    const int lane = lane_id();
+    const bool inm = (mask >> lane) & 1u;
+    const uint32_t i0 = sz + (uint32_t)pos;
+    if (inm) h[i0] = e;
+    __syncwarp();
+    const bool need = inm && i0 > 0 && h[(i0 - 1) >> 5] > e;
+    unsigned nm = __ballot_sync(0xffffffffu, need);
+    if (nm) {
+        if (lane == 0) {
+            while (nm) {
+                const int j = __ffs(nm) - 1;
+                nm &= nm - 1;
+                uint32_t i = sz + __popc(mask & ((1u << j) - 1));
+                const uint64_t val = h[i];
+                while (i > 0) {
+                    const uint32_t pi = (i - 1) >> 5;
+                    const uint64_t pv = h[pi];
+                    if (pv <= val) break;
+                    h[i] = pv;
+                    i = pi;
+                }
+                h[i] = val;
+            }
+        }
+    }
+    sz += __popc(mask);
     __syncwarp();
 }
 
@@ -369,52 +396,35 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// distances of m rows already staged in shared memory (row j at stage + j*vb)
+// squared distance of one row in shared memory to the query, by one lane
 template <int DT>
-__device__ void stage_distances(const uint8_t *stage, const uint8_t *qbytes, int vb, int m, uint32_t *ckey) {
-    const int lane = lane_id();
+__device__ __forceinline__ uint32_t row_key_smem(const uint8_t *row, const uint8_t *qbytes, int vb) {
+    const uint4 *r = (const uint4 *)row, *qv = (const uint4 *)qbytes;
     const int nc = vb >> 4;
-    int G = 1;
-    while (G * 2 <= nc && G * 2 <= 32) G *= 2;
-    const int per_round = 32 / G;
-    const int lig = lane & (G - 1);
-    const int grp = lane / G;
-    const uint4 *qv = (const uint4 *)qbytes;
-    for (int base = 0; base < m; base += per_round) {
-        const int j = base + grp;
-        uint32_t acc = 0;
+    if (DT == ANN_U8) {
+        uint32_t a0 = 0, a1 = 0;
+#pragma unroll 4
+        for (int c = 0; c < nc; c++) {
+            const uint4 a = r[c], q = qv[c];
+            const uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
+            const uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
+            a0 = __dp4a(d0, d0, a0);
+            a1 = __dp4a(d1, d1, a1);
+            a0 = __dp4a(d2, d2, a0);
+            a1 = __dp4a(d3, d3, a1);
+        }
+        return a0 + a1;
+    } else {
         float hi = 0.f, lo = 0.f;
-        if (j < m) {
-            const uint4 *row = (const uint4 *)(stage + (size_t)j * vb);
-            for (int c = lig; c < nc; c += G) {
-                const uint4 a = row[c], q = qv[c];
-                if (DT == ANN_U8) {
-                    uint32_t d0 = __vabsdiffu4(a.x, q.x), d1 = __vabsdiffu4(a.y, q.y);
-                    uint32_t d2 = __vabsdiffu4(a.z, q.z), d3 = __vabsdiffu4(a.w, q.w);
-                    acc = __dp4a(d0, d0, acc);
-                    acc = __dp4a(d1, d1, acc);
-                    acc = __dp4a(d2, d2, acc);
-                    acc = __dp4a(d3, d3, acc);
-                } else {
-                    df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
-                    df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
-                }
-            }
+        for (int c = 0; c < nc; c++) {
+            const uint4 a = r[c], q = qv[c];
+            df_acc_sqdiff(__uint_as_float(a.x), __uint_as_float(q.x), hi, lo);
+            df_acc_sqdiff(__uint_as_float(a.y), __uint_as_float(q.y), hi, lo);
+            df_acc_sqdiff(__uint_as_float(a.z), __uint_as_float(q.z), hi, lo);
+            df_acc_sqdiff(__uint_as_float(a.w), __uint_as_float(q.w), hi, lo);
         }
-        for (int off = G >> 1; off > 0; off >>= 1) {
-            if (DT == ANN_U8) {
-                acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            } else {
-                float h2 = __shfl_xor_sync(0xffffffffu, hi, off);
-                float l2 = __shfl_xor_sync(0xffffffffu, lo, off);
-                df_add(hi, lo, h2, l2);
-            }
-        }
-        if (j < m && lig == 0) ckey[j] = DT == ANN_U8 ? acc : __float_as_uint(__fadd_rn(hi, lo));
+        return __float_as_uint(__fadd_rn(hi, lo));
     }
-    __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -986,14 +996,10 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     int32_t nx_row = -1, sp_row = -1;
     bool nx_vec = false, cp_out = false;
     unsigned nx_mask = 0;
+    uint32_t nx_slot = kNone;  // where this lane's staged id goes in the visited set
     const int vbytes = ix.d * (DT == ANN_U8 ? 1 : 4);
-    // staged rows are handled by groups of sG lanes (16-byte chunks of a row)
-    const int snc = vbytes >> 4;
-    int sG = 1;
-    while (sG * 2 <= snc && sG * 2 <= 32) sG *= 2;
-    const int sper = 32 / sG, slig = lane & (sG - 1), sgrp = lane / sG;
+    const int snc = vbytes >> 4;  // 16-byte chunks per row
     uint8_t *stage = smem + L.stage;
-    int32_t *sid = (int32_t *)(smem + L.sid);
 
     while (t < T) {
         if (bcur >= bcnt && (!ws.exhausted || (WIN && ws.gpos < ws.gcnt))) {
@@ -1093,37 +1099,47 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
             have_key = true;
             n_brpops++;
         }
+        // the new references of this adjacency list, in list order, cut to the budget
         unsigned mask;
+        uint32_t slot = kNone;
         if (staged) {
             mask = nx_mask;  // computed one step earlier against the same visited set and budget
+            slot = nx_slot;
         } else {
-            bool isnew = lane < alen && x >= 0 && x < ix.N && !hash_has(H, L.hash_log, (uint32_t)x);
+            bool isnew = false;
+            if (lane < alen && x >= 0 && x < ix.N) isnew = !hash_find(H, L.hash_log, (uint32_t)x, slot);
             mask = __ballot_sync(0xffffffffu, isnew);
             int room = T - t;
             while (__popc(mask) > room) mask &= ~(1u << (31 - __clz(mask)));  // keep the first `room` in list order
         }
         const int m = __popc(mask);
+        const bool inm = (mask >> lane) & 1u;
+        const int pos = __popc(mask & ((1u << lane) - 1));
         uint64_t mine = ~0ull;
         if (m > 0) {
-            if ((mask >> lane) & 1u) {
-                int pos = __popc(mask & ((1u << lane) - 1));
-                cand[pos] = (uint32_t)x;
-                if (have_key) ckey[pos] = xkey;
-                hash_add(H, L.hash_log, (uint32_t)x);
-            }
+            // mark them visited: the lowest lane among those whose probe ended on
+            // the same empty slot stores there; the others insert by CAS after it
+            const unsigned peers = __match_any_sync(0xffffffffu, inm ? slot : 0xfffffffeu);
+            const bool direct = inm && slot != kNone && (peers & ((1u << lane) - 1)) == 0;
+            if (direct) H[slot] = (uint32_t)x + 1;
             __syncwarp();
+            if (inm && !direct) hash_add(H, L.hash_log, (uint32_t)x);
+            uint32_t key = xkey;
             if (!have_key) {
                 if (staged) {
                     cp_async_wait_all();
                     cp_out = false;
                     __syncwarp();
-                    stage_distances<DT>(stage, qb, vbytes, m, ckey);
+                    if (inm) key = row_key_smem<DT>(stage + (size_t)pos * L.stage_stride, qb, vbytes);
                 } else {
+                    if (inm) cand[pos] = (uint32_t)x;
+                    __syncwarp();
                     cand_distances<DT>(ix, qb, cand, m, ckey);
+                    if (inm) key = ckey[pos];
                 }
             }
-            mine = lane < m ? (((uint64_t)ckey[lane] << 32) | cand[lane]) : ~0ull;
-            heap_push_batch(heap, hsz, mine, m);
+            mine = inm ? (((uint64_t)key << 32) | (uint32_t)x) : ~0ull;
+            heap_push_masked(heap, hsz, mine, mask, pos);
             if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
         }
         // The next pop is known now.  When it is a reference, take its kNN row
@@ -1143,25 +1159,24 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                 // refill first) and no bridge-window entries are still pending
                 const bool refill_next = bcur >= bcnt && (!ws.exhausted || (WIN && ws.gpos < ws.gcnt));
                 if (L.stage_rows && !refill_next && bcur >= wstart + wcnt) {
-                    const bool nw = lane < R && nx_row >= 0 && nx_row < ix.N &&
-                                    !hash_has(H, L.hash_log, (uint32_t)nx_row);
+                    uint32_t s2 = kNone;
+                    bool nw = false;
+                    if (lane < R && nx_row >= 0 && nx_row < ix.N)
+                        nw = !hash_find(H, L.hash_log, (uint32_t)nx_row, s2);
                     unsigned mk = __ballot_sync(0xffffffffu, nw);
                     const int room2 = T - (t + m);
                     while (__popc(mk) > room2) mk &= ~(1u << (31 - __clz(mk)));
                     nx_mask = mk;
+                    nx_slot = s2;
                     nx_vec = true;
-                    if (mk) {
-                        if ((mk >> lane) & 1u) sid[__popc(mk & ((1u << lane) - 1))] = nx_row;
-                        __syncwarp();
-                        const int m2 = __popc(mk);
-                        for (int j = sgrp; j < m2; j += sper) {
-                            const uint8_t *src = (const uint8_t *)ix.X + (int64_t)sid[j] * vbytes;
-                            uint8_t *dst = stage + (size_t)j * vbytes;
-                            for (int c = slig; c < snc; c += sG) cp_async16(dst + 16 * c, src + 16 * c);
-                        }
-                        cp_async_commit();
-                        cp_out = true;
+                    if ((mk >> lane) & 1u) {
+                        // each lane copies its own row into its rank's slot
+                        const uint8_t *src = (const uint8_t *)ix.X + (int64_t)nx_row * vbytes;
+                        uint8_t *dst = stage + (size_t)__popc(mk & ((1u << lane) - 1)) * L.stage_stride;
+                        for (int c = 0; c < snc; c++) cp_async16(dst + 16 * c, src + 16 * c);
                     }
+                    cp_async_commit();
+                    cp_out = mk != 0;
                 }
             }
         }
@@ -1170,7 +1185,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         if (rsmall) {
             if (k > 0) {
                 uint64_t kth = __shfl_sync(0xffffffffu, rreg, k - 1);  // ~0 while fewer than k
-                unsigned pm = __ballot_sync(0xffffffffu, lane < m && mine < kth);
+                unsigned pm = __ballot_sync(0xffffffffu, inm && mine < kth);
                 while (pm) {
                     int j = __ffs(pm) - 1;
                     pm &= pm - 1;
@@ -1185,8 +1200,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                 }
             }
         } else {
-            for (int j = 0; j < m; j++) {
-                uint64_t e = ((uint64_t)ckey[j] << 32) | cand[j];
+            for (unsigned pm = mask; pm; pm &= pm - 1) {
+                const uint64_t e = __shfl_sync(0xffffffffu, mine, __ffs(pm) - 1);
                 if ((int)rlen == k && e >= rbuf[k - 1]) continue;
                 // position = number of entries smaller than e
                 int cntless = 0;
