@@ -442,11 +442,11 @@ struct WalkState {
 
 // Emit the composite (key << 32 | packed ranks) of every non-empty bridge with
 // lo < composite <= hi (lo ignored when first).  Returns how many there were;
-// only the first bcap are stored.  Two phases per chunk: (1) the prefix
+// only the first ocap are stored.  Two phases per chunk: (1) the prefix
 // nodes (c0[, c1]) whose lower bound fits the window and that hold bridges
 // are collected into a node list; (2) the suffix leaves of the listed nodes
 // are processed as one flat range, 32 consecutive leaves per step.
-template <int DT>
+template <int DT, int UL>
 __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
                          uint64_t hi, uint64_t *okey, uint32_t *oval,
                          uint32_t ocap) {
@@ -570,30 +570,45 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
             __syncwarp();
             const uint32_t lt = run;
             uint32_t np = 0;  // running node pointer of this lane
-            for (uint32_t g = lane; g < lt; g += 32) {
-                while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
-                uint32_t j = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
-                uint32_t lf = __ldg(ix.leaf + j);
-                // key first; the rank lookups only for keys inside the window
-                uint32_t c2 = 0, c3 = lf, ksuf;
-                if (nsuf == 1) {
-                    ksuf = D[(P - 1) * n + lf];
-                } else {
-                    c2 = pow2n ? (lf >> logn) : lf / n;
-                    c3 = lf - c2 * n;
-                    ksuf = KeyOps<DT>::add(D[2 * n + c2], D[3 * n + c3]);
+            // UL leaves per lane per step, their loads in flight together
+            for (uint32_t g0 = lane; g0 < lt; g0 += 32 * UL) {
+                uint32_t jv[UL], lfv[UL], npv[UL];
+#pragma unroll
+                for (int u = 0; u < UL; u++) {
+                    const uint32_t g = g0 + 32 * u;
+                    jv[u] = 0xffffffffu;
+                    if (g < lt) {
+                        while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
+                        npv[u] = np;
+                        jv[u] = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
+                        lfv[u] = __ldg(ix.leaf + jv[u]);
+                    }
                 }
-                uint32_t key = KeyOps<DT>::add(nodes[4 * np + 2], ksuf);
-                if (key > hik || (!first && key < (uint32_t)(lo >> 32))) continue;
-                uint32_t rsuf = nsuf == 1 ? (uint32_t)rk[(P - 1) * n + lf]
-                                          : (((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3]);
-                uint32_t ranks = (nodes[4 * np + 3] << (8 * nsuf)) | rsuf;
-                uint64_t comp = ((uint64_t)key << 32) | ranks;
-                if (comp <= hi && (first || comp > lo)) {
-                    uint32_t s = atomicAdd(&cnt[0], 1u);
-                    if (s < ocap) {
-                        okey[s] = comp;
-                        oval[s] = j;
+#pragma unroll
+                for (int u = 0; u < UL; u++) {
+                    if (jv[u] == 0xffffffffu) continue;
+                    const uint32_t j = jv[u], lf = lfv[u], nq = npv[u];
+                    // key first; the rank lookups only for keys inside the window
+                    uint32_t c2 = 0, c3 = lf, ksuf;
+                    if (nsuf == 1) {
+                        ksuf = D[(P - 1) * n + lf];
+                    } else {
+                        c2 = pow2n ? (lf >> logn) : lf / n;
+                        c3 = lf - c2 * n;
+                        ksuf = KeyOps<DT>::add(D[2 * n + c2], D[3 * n + c3]);
+                    }
+                    const uint32_t key = KeyOps<DT>::add(nodes[4 * nq + 2], ksuf);
+                    if (key > hik || (!first && key < (uint32_t)(lo >> 32))) continue;
+                    const uint32_t rsuf = nsuf == 1 ? (uint32_t)rk[(P - 1) * n + lf]
+                                                    : (((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3]);
+                    const uint32_t ranks = (nodes[4 * nq + 3] << (8 * nsuf)) | rsuf;
+                    const uint64_t comp = ((uint64_t)key << 32) | ranks;
+                    if (comp <= hi && (first || comp > lo)) {
+                        const uint32_t s = atomicAdd(&cnt[0], 1u);
+                        if (s < ocap) {
+                            okey[s] = comp;
+                            oval[s] = j;
+                        }
                     }
                 }
             }
@@ -631,7 +646,7 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
     const int lane = lane_id();
     while (!ws.exhausted) {
         uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
-        uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, bkey, bidx, L.bcap);
+        uint32_t c = walk<DT, 1>(ix, smem, L, ws.lo, ws.first, hi, bkey, bidx, L.bcap);
         if (c > L.bcap) {
             // too many in the window: halve it (in composite space)
             uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
@@ -645,7 +660,7 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
             // width 1 key unit: split the composite range directly
             uint64_t h2 = base + span / 2;
             while (true) {
-                c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, bkey, bidx, L.bcap);
+                c = walk<DT, 1>(ix, smem, L, ws.lo, ws.first, h2, bkey, bidx, L.bcap);
                         if (c <= L.bcap) break;
                 span = h2 - base;
                 if (span == 0) { cap_err = true; return 0; }
@@ -762,7 +777,7 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
         ws.gpos = ws.gcnt = 0;
         while (!ws.exhausted) {
             uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
-            uint32_t c = walk<DT>(ix, smem, L, ws.lo, ws.first, hi, gk0, gv0, gcap);
+            uint32_t c = walk<DT, 4>(ix, smem, L, ws.lo, ws.first, hi, gk0, gv0, gcap);
                 if (c > gcap) {
                 // too many in the window: halve it (in composite space)
                 uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
@@ -774,7 +789,7 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
                 }
                 uint64_t h2 = base + span / 2;
                 while (true) {
-                    c = walk<DT>(ix, smem, L, ws.lo, ws.first, h2, gk0, gv0, gcap);
+                    c = walk<DT, 4>(ix, smem, L, ws.lo, ws.first, h2, gk0, gv0, gcap);
                                 if (c <= gcap) break;
                     span = h2 - base;
                     if (span == 0) { cap_err = true; return 0; }
