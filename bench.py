@@ -452,6 +452,22 @@ def main():
                 and pj.get("kernel_source_sha256") == digest):
             traffic = pj.get("dram_bytes_per_launch")
 
+    # uneven batch: per-query budgets T90/4, T90/2, T90 (plain sizes for the largest; persistent buckets)
+    mix_choices = sorted({max(32, T90 // 4), max(32, T90 // 2), T90})
+    T_mix = torch.from_numpy(datagen.uneven_budgets(WORKLOAD, nq, mix_choices)).cuda()
+
+    def step_mix(mode):
+        ann.ann_search_batch(index, Q, K, T_mix, kmax=K, mode=mode, out_ids=out_ids, out_keys=out_keys,
+                             out_status=out_st, stream=stream)
+
+    t_mix_plain = time_steps(torch, lambda: step_mix(0), args.steps, args.warmup, flush, stream)
+    t_mix_pers = time_steps(torch, lambda: step_mix(1), args.steps, args.warmup, flush, stream)
+    uneven = {"T_choices": mix_choices, "k": K,
+              "plain_qps": nq * args.steps / (sum(t_mix_plain) / 1e3),
+              "persistent_qps": nq * args.steps / (sum(t_mix_pers) / 1e3)}
+    log(f"uneven budgets {mix_choices}: plain {uneven['plain_qps']:.0f} q/s, "
+        f"persistent {uneven['persistent_qps']:.0f} q/s")
+
     # end to end through the C ABI with pinned host buffers
     q_host = torch.empty_like(Q, device="cpu").pin_memory()
     q_host.copy_(Q.cpu())
@@ -507,6 +523,7 @@ def main():
             "plain": {"qps": plain_qps, "ms_per_step": statistics.mean(t_plain)},
             "persistent": {"qps": value / ws, "ms_per_step": ms_per_step},
             "served": served,
+            "uneven": uneven,
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.numel()),
                     "d2h_bytes_per_step": int(nq * K * 8)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -50,7 +50,7 @@ constexpr uint32_t kStageBytes = 4096;
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
-                                                  int kmax, int bcap, int b, int R) {
+                                                  int kmax, int bcap, int b, int R, bool stage = true) {
     WarpLayout L;
     uint32_t o = 0;
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
@@ -80,7 +80,7 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     // the walk (prefix sums + node list), the bridge window (reference ids +
     // keys) and the staged neighbour vectors of the next pop
     const uint32_t vb = (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u);
-    L.stage_rows = (uint32_t)R * vb <= kStageBytes ? (uint32_t)R : 0u;
+    L.stage_rows = stage && (uint32_t)R * vb <= kStageBytes ? (uint32_t)R : 0u;
     L.ncap = 64;
     const uint32_t walk_bytes = align_up(4u * (n + 1), 16) + 16u * L.ncap;
     const uint32_t win_bytes = 2u * align_up(4u * wb, 16);
@@ -1333,6 +1333,7 @@ static const int kWindowedFromT = 1024;
 struct Tune {
     int warps;
     int bcap;
+    bool stage;  // stage the next pop's neighbour vectors (cp.async)
 };
 
 // Warps per CTA: the count that keeps the most warps resident per SM given
@@ -1341,6 +1342,7 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     Tune t;
     // bridge batch: budgets below the windowed kernels pop few bridges
     t.bcap = capT >= kWindowedFromT ? 128 : 64;
+    t.stage = true;
     WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b, ix.R);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
@@ -1389,12 +1391,14 @@ struct LaunchCfg {
 };
 
 static int plan_launch(const SearchArgs &base, int capT, bool persistent, const int32_t *list,
-                       const int32_t *list_count, int64_t list_len, int32_t *ticket, LaunchCfg &cfg) {
+                       const int32_t *list_count, int64_t list_len, int32_t *ticket, LaunchCfg &cfg,
+                       const Tune *tune = nullptr) {
     SearchArgs A = base;
     A.capT = capT;
-    Tune tn = choose_tune(A.ix, capT, A.kmax);
+    const Tune tn = tune ? *tune : choose_tune(A.ix, capT, A.kmax);
     A.bcap = tn.bcap;
-    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b, A.ix.R);
+    A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b, A.ix.R,
+                      tn.stage);
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
@@ -1504,6 +1508,7 @@ struct PlanKey {
 struct PlanCache {
     std::mutex mu;
     std::map<PlanKey, Plan> plans;
+    std::map<std::pair<int, int>, Tune> tuned;  // (bucket capacity, kmax) -> measured best launch shape
 };
 
 void free_plans(ann_index *ix) {
@@ -1528,25 +1533,168 @@ static void bucket_range(const int32_t *T, int32_t T_all, int &b0, int &b1) {
     b0 = T ? 0 : b1;
 }
 
-static int record_persistent(const SearchArgs &A, int64_t nq, const int32_t *T, int32_t T_all,
-                             int32_t *scratch, uint8_t *wscratch, cudaStream_t s) {
+static const Tune *tuned_for(const PlanCache *pc, int capT, int kmax) {
+    auto it = pc->tuned.find({capT, kmax});
+    return it == pc->tuned.end() ? nullptr : &it->second;
+}
+
+static int bucket_cap(int bkt) { return (128 << bkt) > kMaxT ? kMaxT : (128 << bkt); }
+
+// One replay of the persistent form.  A uniform budget is one bucket and the
+// queries are taken in order; otherwise a device pass sorts them into
+// buckets first.  Every bucket's kernel pulls its queries from a ticket.
+// Buckets without global scratch run concurrently on forked streams (largest
+// budget first), so the smaller ones fill the SMs the larger leave idle at
+// their tail; windowed buckets share one scratch and run one after another.
+// streams and events of the fork/join; they must outlive the capture
+struct ForkSet {
+    cudaStream_t side[kBuckets] = {};
+    cudaEvent_t fork = nullptr, join[kBuckets] = {};
+    int nside = 0;
+    ~ForkSet() {
+        for (int i = 0; i < nside; i++) {
+            if (join[i]) cudaEventDestroy(join[i]);
+            if (side[i]) cudaStreamDestroy(side[i]);
+        }
+        if (fork) cudaEventDestroy(fork);
+    }
+};
+
+static int record_persistent(const PlanCache *pc, const SearchArgs &A, int64_t nq, const int32_t *T, int32_t T_all,
+                             int32_t *scratch, uint8_t *wscratch, cudaStream_t s, ForkSet &fs) {
     int32_t *counts = scratch, *tickets = scratch + kBuckets, *lists = scratch + 2 * kBuckets;
     ANN_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2 * kBuckets, s));
-    if (nq > 0) {
+    if (T) {
         bucket_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, T, T_all, counts, lists, tickets);
         ANN_CUDA(cudaGetLastError());
     }
     int b0, b1;
     bucket_range(T, T_all, b0, b1);
-    for (int bkt = b0; bkt <= b1; bkt++) {
-        int capT = 128 << bkt;
-        if (capT > kMaxT) capT = kMaxT;
+    int rc = ANN_OK;
+    for (int bkt = b1; bkt >= b0 && rc == ANN_OK; bkt--) {
+        const int capT = bucket_cap(bkt);
         LaunchCfg cfg;
-        int r = plan_launch(A, capT, true, lists + (int64_t)bkt * nq, counts + bkt, nq, tickets + bkt, cfg);
-        if (r == ANN_OK) r = do_launch(cfg, wscratch, s);  // buckets run one after another: shared scratch
-        if (r != ANN_OK) return r;
+        rc = T ? plan_launch(A, capT, true, lists + (int64_t)bkt * nq, counts + bkt, nq, tickets + bkt, cfg,
+                             tuned_for(pc, capT, A.kmax))
+               : plan_launch(A, capT, true, nullptr, nullptr, nq, tickets + bkt, cfg, tuned_for(pc, capT, A.kmax));
+        if (rc != ANN_OK) break;
+        if (cfg.win || b0 == b1) {
+            rc = do_launch(cfg, wscratch, s);
+            continue;
+        }
+        if (!fs.fork) {
+            if (cudaEventCreateWithFlags(&fs.fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(fs.fork, s) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "fork event");
+                break;
+            }
+        }
+        const int i = fs.nside;
+        if (cudaStreamCreateWithFlags(&fs.side[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fs.join[i], cudaEventDisableTiming) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "side stream");
+            break;
+        }
+        fs.nside++;
+        if (cudaStreamWaitEvent(fs.side[i], fs.fork, 0) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "fork");
+            break;
+        }
+        rc = do_launch(cfg, nullptr, fs.side[i]);
+        if (rc != ANN_OK) break;
+        if (cudaEventRecord(fs.join[i], fs.side[i]) != cudaSuccess || cudaStreamWaitEvent(s, fs.join[i], 0) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "join");
+            break;
+        }
     }
-    return ANN_OK;
+    return rc;
+}
+
+// Launch shapes worth measuring for a bucket: the analytic choice, fewer warps
+// per CTA (finer CTA granularity, fewer registers per SM in use), and the
+// analytic choice without cp.async staging.  All give identical results.
+static std::vector<Tune> tune_candidates(const DevIndex &ix, int capT, int kmax) {
+    const Tune d = choose_tune(ix, capT, kmax);
+    std::vector<Tune> c{d};
+    for (int w : {1, 2, 3, 4})
+        if (w < d.warps) c.push_back(Tune{w, d.bcap, true});
+    c.push_back(Tune{d.warps, d.bcap, false});
+    return c;
+}
+
+// Measure the candidates of every bucket this batch uses that has no measured
+// choice yet, on (a prefix of) the batch itself, and keep the fastest.
+static int autotune(PlanCache *pc, const SearchArgs &A, int64_t nq, const int32_t *T, int32_t T_all,
+                    int32_t *scratch, cudaStream_t s) {
+    int b0, b1;
+    bucket_range(T, T_all, b0, b1);
+    bool todo = false;
+    for (int bkt = b0; bkt <= b1; bkt++) todo |= tuned_for(pc, bucket_cap(bkt), A.kmax) == nullptr;
+    if (!todo) return ANN_OK;
+    int32_t *counts = scratch, *tickets = scratch + kBuckets, *lists = scratch + 2 * kBuckets;
+    int32_t *tcount = scratch + kBuckets * (2 + nq);  // one extra word: queries per tuning run
+    ANN_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * 2 * kBuckets, s));
+    int32_t hc[kBuckets] = {0};
+    if (T) {
+        bucket_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(nq, T, T_all, counts, lists, tickets);
+        ANN_CUDA(cudaGetLastError());
+        ANN_CUDA(cudaMemcpyAsync(hc, counts, sizeof(hc), cudaMemcpyDeviceToHost, s));
+        ANN_CUDA(cudaStreamSynchronize(s));
+    } else {
+        hc[b1] = (int32_t)nq;
+    }
+    cudaEvent_t e0, e1;
+    ANN_CUDA(cudaEventCreate(&e0));
+    ANN_CUDA(cudaEventCreate(&e1));
+    int rc = ANN_OK;
+    for (int bkt = b0; bkt <= b1 && rc == ANN_OK; bkt++) {
+        const int capT = bucket_cap(bkt);
+        if (tuned_for(pc, capT, A.kmax) || hc[bkt] == 0) continue;
+        const std::vector<Tune> cands = tune_candidates(A.ix, capT, A.kmax);
+        // tune on up to four rounds of the default shape's resident warps
+        LaunchCfg c0;
+        rc = plan_launch(A, capT, true, nullptr, nullptr, nq, tickets + bkt, c0, &cands[0]);
+        if (rc != ANN_OK) break;
+        const int64_t resident = (int64_t)c0.grid.x * (c0.block.x / 32);
+        const int32_t ntune = (int32_t)std::min<int64_t>(hc[bkt], 4 * resident);
+        ANN_CUDA(cudaMemcpyAsync(tcount, &ntune, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        const int32_t *list = T ? lists + (int64_t)bkt * nq : nullptr;
+        float best_ms = 0.f;
+        int best = -1;
+        for (size_t ci = 0; ci < cands.size() && rc == ANN_OK; ci++) {
+            float ms_min = 0.f;
+            for (int rep = 0; rep < 2; rep++) {
+                LaunchCfg cfg;
+                if (plan_launch(A, capT, true, list, tcount, nq, tickets + bkt, cfg, &cands[ci]) != ANN_OK) break;
+                uint8_t *ws = nullptr;
+                if (cfg.scratch_bytes && cudaMallocAsync((void **)&ws, cfg.scratch_bytes, s) != cudaSuccess) break;
+                cudaMemsetAsync(tickets + bkt, 0, sizeof(int32_t), s);
+                cudaEventRecord(e0, s);
+                rc = do_launch(cfg, ws, s);
+                cudaEventRecord(e1, s);
+                if (ws) cudaFreeAsync(ws, s);
+                if (rc != ANN_OK) break;
+                cudaError_t ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) {
+                    rc = cuda_fail(ce, "autotune run");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 0 || ms < ms_min) ms_min = ms;
+                if (ms > 50.f) break;  // long runs: one measurement is enough
+            }
+            if (rc == ANN_OK && ms_min > 0.f && (best < 0 || ms_min < best_ms)) {
+                best_ms = ms_min;
+                best = (int)ci;
+            }
+        }
+        cudaGetLastError();  // a candidate that failed to configure is simply not chosen
+        if (rc == ANN_OK) pc->tuned[{capT, A.kmax}] = cands[best < 0 ? 0 : best];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
@@ -1629,14 +1777,20 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
     auto it = pc->plans.find(key);
     if (it == pc->plans.end()) {
         Plan p;
-        ANN_CUDA(cudaMalloc(&p.scratch, sizeof(int32_t) * (2 * kBuckets + (size_t)kBuckets * nq)));
+        ANN_CUDA(cudaMalloc(&p.scratch, sizeof(int32_t) * (2 * kBuckets + (size_t)kBuckets * nq + 1)));
         {
+            int r = autotune(pc, A, nq, T, T_all, p.scratch, s);
+            if (r != ANN_OK) {
+                cudaFree(p.scratch);
+                return r;
+            }
             size_t need = 0;
             int b0, b1;
             bucket_range(T, T_all, b0, b1);
             for (int bkt = b0; bkt <= b1; bkt++) {
                 LaunchCfg cfg;
-                int r = plan_launch(A, 128 << bkt, true, nullptr, p.scratch, nq, p.scratch, cfg);
+                r = plan_launch(A, bucket_cap(bkt), true, nullptr, p.scratch, nq, p.scratch, cfg,
+                                tuned_for(pc, bucket_cap(bkt), kmax));
                 if (r != ANN_OK) {
                     cudaFree(p.scratch);
                     return r;
@@ -1655,10 +1809,16 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
         ANN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
         ANN_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        int rr = record_persistent(A, nq, T, T_all, p.scratch, p.wscratch, cap);
-        cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+        cudaError_t ce;
+        int rr;
+        {
+            ForkSet fs;
+            rr = record_persistent(pc, A, nq, T, T_all, p.scratch, p.wscratch, cap, fs);
+            ce = cudaStreamEndCapture(cap, &graph);
+        }
         cudaStreamDestroy(cap);
         if (rr != ANN_OK || ce != cudaSuccess) {
+            if (ce == cudaSuccess) cudaGraphDestroy(graph);
             cudaFree(p.scratch);
             if (p.wscratch) cudaFree(p.wscratch);
             return rr != ANN_OK ? rr : cuda_fail(ce, "cudaStreamEndCapture");

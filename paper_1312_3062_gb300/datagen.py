@@ -126,6 +126,12 @@ def per_query_params(workload: int, nq: int, seed_salt: int = 20):
     return k, T
 
 
+def uneven_budgets(workload: int, nq: int, choices, seed_salt: int = 40) -> np.ndarray:
+    """Per-query budgets drawn uniformly from `choices` (an uneven batch)."""
+    rng = np.random.Generator(np.random.PCG64(_seq(workload, seed_salt)))
+    return rng.choice(np.asarray(choices, np.int32), size=nq).astype(np.int32)
+
+
 def mixture(seed: int, N: int, d: int, ncomp: int, dtype) -> np.ndarray:
     """Small seeded mixtures for parity cases: uint8 rows as in workload 1
     (means U[0,255], sigma 20, rint + clip), float32 rows as in workload 3

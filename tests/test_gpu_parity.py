@@ -274,3 +274,23 @@ def test_index_save_load_roundtrip(ann, tiny_sift, tmp_path):
     b = ann.ann_search_batch(ix2, dev(Q), 10, 256)[0].cpu().numpy()
     np.testing.assert_array_equal(a, b)
     assert ix2.info()["M"] == len(bg["bridges"])
+
+
+def test_persistent_autotuned_plans_equal_oracle(ann, tiny_sift):
+    # three budget buckets in one batch: the first persistent call measures
+    # launch shapes per bucket on the batch itself; a second plan (new output
+    # buffers) reuses the measured shapes; plain and both persistent plans
+    # equal the oracle
+    X, Q, G, C, bg = tiny_sift
+    rng = np.random.default_rng(17)
+    T = rng.choice(np.array([100, 200, 400], np.int32), size=len(Q)).astype(np.int32)
+    wi, wk, _ = oracle.search(X, G, C, bg, Q, 10, T, kmax=10, nthreads=8)
+    ix = ann.Index.create(dev(X), dev(G), dev(C), t=100, b=5, bridges=bg)
+    Qd, Td = dev(Q), dev(T)
+    for mode in (0, 1, 1):
+        ids, keys, st = ann.ann_search_batch(ix, Qd, 10, Td, kmax=10, mode=mode)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        np.testing.assert_array_equal(ids.cpu().numpy(), wi)
+        assert_keys(gpu_keys(keys, np.uint8), wk, np.uint8)
+    ix.free()
