@@ -67,7 +67,11 @@ __device__ __forceinline__ void merge_row(uint64_t &mine, const uint32_t *drow, 
 template <int DT>
 __global__ void __launch_bounds__(KB_THREADS) knn_kernel(const void *refs, int64_t N, const void *queries, int64_t nq,
                                                        int d, int k, int exclude_self, const uint32_t *rnorm,
-                                                       const uint32_t *qnorm, int32_t *out_ids, uint32_t *out_keys) {
+                                                       const uint32_t *qnorm, int32_t *out_ids, uint32_t *out_keys,
+                                                       const int32_t *qsel = nullptr) {
+    // qsel (optional): the tile's row i is query row qsel[i] (its id for
+    // exclude_self and its output row); otherwise row i itself
+#define QROW(i) (qsel ? (int64_t)qsel[(i)] : (int64_t)(i))
     extern __shared__ __align__(16) uint8_t sm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * KB_M;
@@ -91,9 +95,9 @@ __global__ void __launch_bounds__(KB_THREADS) knn_kernel(const void *refs, int64
         const int words = d / 4;
         for (int i = tid; i < KB_M * words; i += KB_THREADS) {
             int r = i / words, w = i % words;
-            As[r * SW + w] = r < qrows ? __ldg((const uint32_t *)((const uint8_t *)queries + (q0 + r) * d) + w) : 0u;
+            As[r * SW + w] = r < qrows ? __ldg((const uint32_t *)((const uint8_t *)queries + QROW(q0 + r) * d) + w) : 0u;
         }
-        for (int r = tid; r < KB_M; r += KB_THREADS) qn[r] = r < qrows ? qnorm[q0 + r] : 0u;
+        for (int r = tid; r < KB_M; r += KB_THREADS) qn[r] = r < qrows ? qnorm[QROW(q0 + r)] : 0u;
     }
     for (int64_t r0 = 0; r0 < N; r0 += KB_N) {
         const int nvalid = (int)(N - r0 < KB_N ? N - r0 : KB_N);
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(KB_THREADS) knn_kernel(const void *refs, int64
                 __syncthreads();
                 for (int i = tid; i < KB_M * 64; i += KB_THREADS) {
                     int r = i / 64, w = i % 64;
-                    As[r * SW + w] = (r < qrows && w < kc) ? __float_as_uint(__ldg(Q + (q0 + r) * d + k0 + w)) : 0u;
+                    As[r * SW + w] = (r < qrows && w < kc) ? __float_as_uint(__ldg(Q + QROW(q0 + r) * d + k0 + w)) : 0u;
                 }
                 for (int i = tid; i < KB_N * 64; i += KB_THREADS) {
                     int r = i / 64, w = i % 64;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(KB_THREADS) knn_kernel(const void *refs, int64
         for (int rr = 0; rr < KB_M / 8; rr++) {
             int r = warp * (KB_M / 8) + rr;
             if (r < qrows)
-                merge_row(mine[rr], &Ds[r * (KB_N + 1)], r0, nvalid, exclude_self ? q0 + r : -1, k);
+                merge_row(mine[rr], &Ds[r * (KB_N + 1)], r0, nvalid, exclude_self ? QROW(q0 + r) : -1, k);
         }
     }
 #pragma unroll
@@ -189,12 +193,31 @@ __global__ void __launch_bounds__(KB_THREADS) knn_kernel(const void *refs, int64
         if (r < qrows && lane < k) {
             uint64_t v = mine[rr];
             bool have = v != ~0ull;
-            out_ids[(q0 + r) * k + lane] = have ? (int32_t)(uint32_t)v : -1;
+            out_ids[QROW(q0 + r) * k + lane] = have ? (int32_t)(uint32_t)v : -1;
             if (out_keys)
-                out_keys[(q0 + r) * k + lane] = have ? (uint32_t)(v >> 32) : (DT == ANN_U8 ? 0xffffffffu : 0x7f800000u);
+                out_keys[QROW(q0 + r) * k + lane] =
+                    have ? (uint32_t)(v >> 32) : (DT == ANN_U8 ? 0xffffffffu : 0x7f800000u);
         }
     }
+#undef QROW
 }
+
+// exact SIMT k-NN of the selected float32 query rows (fallback of the
+// tensor-core path for rows it cannot certify)
+int knn_f32_rows(const float *refs, int64_t N, const float *queries, const int32_t *rows, int64_t nrows, int d,
+                 int k, int exclude_self, int32_t *out_ids, uint32_t *out_keys, cudaStream_t s) {
+    const int SW = 64 + 4;
+    size_t smem = 4 * ((size_t)(KB_M + KB_N) * SW + (size_t)KB_M * (KB_N + 1) + KB_M + KB_N);
+    ANN_CUDA(cudaFuncSetAttribute(knn_kernel<ANN_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    knn_kernel<ANN_F32><<<(unsigned)((nrows + KB_M - 1) / KB_M), KB_THREADS, smem, s>>>(
+        refs, N, queries, nrows, d, k, exclude_self, nullptr, nullptr, out_ids, out_keys, rows);
+    ANN_CUDA(cudaGetLastError());
+    return ANN_OK;
+}
+
+// implemented in ann_knn_f32.cu
+int knn_f32_tensor(const float *refs, int64_t N, const float *queries, int64_t nq, int d, int k, int exclude_self,
+                   int32_t *out_ids, uint32_t *out_keys, cudaStream_t s);
 
 }  // namespace ann
 
@@ -214,6 +237,10 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
     if (dtype == ANN_U8 && (d == 64 || d == 128))
         return knn_u8_tensor((const uint8_t *)refs, N, (const uint8_t *)queries, nq, d, k, exclude_self, out_ids,
                              (uint32_t *)out_keys, s);
+    // float32 at scale: candidates from tensor-core dot products, exact keys
+    if (dtype == ANN_F32 && N >= 8192 && nq >= 256)
+        return knn_f32_tensor((const float *)refs, N, (const float *)queries, nq, d, k, exclude_self, out_ids,
+                              (uint32_t *)out_keys, s);
     uint32_t *rn = nullptr, *qn = nullptr;
     if (dtype == ANN_U8) {
         ANN_CUDA(cudaMallocAsync((void **)&rn, 4 * N, s));

@@ -294,3 +294,29 @@ def test_persistent_autotuned_plans_equal_oracle(ann, tiny_sift):
         np.testing.assert_array_equal(ids.cpu().numpy(), wi)
         assert_keys(gpu_keys(keys, np.uint8), wk, np.uint8)
     ix.free()
+
+
+@pytest.mark.parametrize("N,d,R", [(12000, 384, 20), (9000, 512, 16)])
+def test_f32_tensor_knn_graph_sampled_rows(ann, N, d, R):
+    # large enough for the tensor-core candidate path (N >= 8192); exact keys
+    X = gmm(500 + d, N, d, 16, np.float32)
+    G, K = ann.ann_build_knn_graph(dev(X), R)
+    G, K = G.cpu().numpy(), K.cpu().numpy()
+    rows = np.random.default_rng(d).choice(N, 64, replace=False)
+    ids, keys = oracle.exact_knn(X, X[rows], R + 1)
+    for i, r in enumerate(rows):
+        keep = ids[i] != r
+        np.testing.assert_array_equal(G[r], ids[i][keep][:R])
+        np.testing.assert_allclose(K[r].astype(np.float64), keys[i][keep][:R], rtol=F32_RTOL, atol=0)
+
+
+def test_f32_tensor_knn_rows_with_many_ties_fall_back_exactly(ann):
+    # 700 copies of one row: its copies' candidate lists overflow and those
+    # rows are recomputed exactly; every row still equals the oracle
+    X = gmm(900, 10000, 64, 8, np.float32)
+    X[1000:1700] = X[1000]
+    Q = np.ascontiguousarray(X[::20])
+    ids, keys = ann.ann_exact_knn(dev(X), dev(Q), 20)
+    want_ids, want_keys = oracle.exact_knn(X, Q, 20)
+    np.testing.assert_array_equal(ids.cpu().numpy(), want_ids)
+    np.testing.assert_allclose(keys.cpu().numpy().astype(np.float64), want_keys, rtol=F32_RTOL, atol=0)
