@@ -73,3 +73,72 @@ def test_sampled_search(sift1m, T, sel):
     assert np.all(gs.cpu().numpy() == 0)
     np.testing.assert_array_equal(gi.cpu().numpy(), wi)
     np.testing.assert_array_equal(gk.cpu().numpy().view(np.uint32).astype(np.float64), wk)
+
+
+# ---------------------------------------------------------------------------
+# GIST-shaped 1M workload: N = 1,000,000 x 384 float32, R = 20, P = 3 x n = 128,
+# per-query k in {1, 10, 100} and T log-uniform in [64, 8192], persistent form
+# ---------------------------------------------------------------------------
+
+F32_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gist1m():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1312_3062_gb300 import _build
+    _build.build()
+    from paper_1312_3062_gb300 import ann
+    spec = datagen.WORKLOADS[3]
+    X = datagen.references(3)
+    Q = datagen.queries(3)
+    rng = np.random.default_rng(3033)
+    train = np.sort(rng.choice(len(X), 20000, replace=False))
+    C = oracle.round_centers(oracle.kmeans(X[train], 3, 128, 5, datagen.kmeans_init_rows(3, 20000, 128)),
+                             np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    G, _ = ann.ann_build_knn_graph(Xd, spec["R"])
+    ix = ann.Index.create(Xd, G, torch.from_numpy(C).cuda(), t=100, b=5)
+    k, T = datagen.per_query_params(3, len(Q))
+    ids, keys, st = ann.ann_search_batch(ix, torch.from_numpy(Q).cuda(), torch.from_numpy(k).cuda(),
+                                         torch.from_numpy(T).cuda(), kmax=100, mode=1)
+    torch.cuda.synchronize()
+    return ann, X, Q, C, G.cpu().numpy(), ix, k, T, ids.cpu().numpy(), keys.cpu().numpy(), st.cpu().numpy()
+
+
+def test_gist1m_sampled_knn_rows(gist1m):
+    ann, X, Q, C, G, ix, *_ = gist1m
+    rows = np.random.default_rng(3).choice(len(X), 32, replace=False)
+    ids, keys = oracle.exact_knn(X, X[rows], 21)
+    for i, r in enumerate(rows):
+        keep = ids[i] != r
+        np.testing.assert_array_equal(G[r], ids[i][keep][:20])
+
+
+gist1m_bg = [None]
+
+
+def test_gist1m_full_bridge_graph(gist1m):
+    ann, X, Q, C, G, ix, *_ = gist1m
+    bg = oracle.bridge_graph(X, C, 100, 5)
+    ids, refs = ix.bridges()
+    np.testing.assert_array_equal(ids, bg["bridges"])
+    np.testing.assert_array_equal(refs[refs >= 0], bg["refs"])
+    gist1m_bg[0] = bg
+
+
+def test_gist1m_sampled_uneven_search(gist1m):
+    # the whole 10,000-query uneven batch ran in the persistent form; sampled
+    # queries with budgets the oracle finishes quickly are checked one by one
+    ann, X, Q, C, G, ix, k, T, ids, keys, st = gist1m
+    assert np.all(st == 0)
+    bg = gist1m_bg[0] if gist1m_bg[0] is not None else oracle.bridge_graph(X, C, 100, 5)
+    small = np.where(T <= 256)[0]
+    sel = np.random.default_rng(33).choice(small, 8, replace=False)
+    wi, wk, _ = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=len(sel))
+    np.testing.assert_array_equal(ids[sel], wi)
+    fin = np.isfinite(wk)
+    got = keys[sel].view(np.float32).astype(np.float64)
+    np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)
+    assert np.all(np.isinf(got[~fin]))
