@@ -57,7 +57,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--build-only", action="store_true", help="build the index and exit (profiling the build)")
-    return ap.parse_args()
+    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
+                    help="2 sift1m (default, the headline); 3 gist1m uneven k/T; 4 hog4m recall-vs-T; "
+                         "5 sift10m served")
+    args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload
+    return args
 
 
 # --------------------------------------------------------------------------
@@ -172,25 +178,44 @@ def build_workload(args, torch, ann, datagen, log):
     log(f"kNN graph {t_knn:.1f}s, k-means {t_km:.1f}s, bridge graph {t_bg:.1f}s")
     info = index.info()
     t0 = time.time()
-    gt_ids, gt_keys = ann.ann_exact_knn(X, Q, K)
+    gt_ids, gt_keys = ann.ann_exact_knn(X, Q, max(K, min(32, max(spec["k"]))))
     torch.cuda.synchronize()
     log(f"ground truth {time.time() - t0:.1f}s; index M={info['M']} alpha={info['alpha']:.3g}")
     return dict(spec=spec, N=N, nq=nq, X=X, Q=Q, Xh=Xh, Qh=Qh, index=index, gt_ids=gt_ids, gt_keys=gt_keys,
                 info=info, G=G, C=C, build_s={"knn_graph": t_knn, "kmeans": t_km, "bridge_graph": t_bg})
 
 
-def recall_at_10(torch, ids, W):
+def recall_at_10(torch, ids, W, k=None):
     """Mean r/k (Sec. 5.1), tie-tolerant: a returned id counts when its true
-    distance is <= the true 10th distance."""
+    distance is <= the true k-th distance.  k: an int (default 10) or a
+    per-query tensor (values up to the ground truth's width)."""
     X, Q, gt_keys = W["X"], W["Q"], W["gt_keys"]
-    kth = gt_keys[:, K - 1].to(torch.int64) & 0xFFFFFFFF
-    ids = ids[:, :K].long()
-    valid = ids >= 0
-    rows = X[ids.clamp(min=0)].to(torch.int32)                 # nq x k x d
-    diff = rows - Q[:, None, :].to(torch.int32)
-    dist = (diff * diff).sum(-1).to(torch.int64)
-    hit = valid & (dist <= kth[:, None])
-    return float(hit.sum().item()) / (K * ids.shape[0])
+    nq = ids.shape[0]
+    if k is None:
+        k = torch.full((nq,), K, dtype=torch.int64, device=ids.device)
+    elif not torch.is_tensor(k):
+        k = torch.full((nq,), int(k), dtype=torch.int64, device=ids.device)
+    k = k.to(torch.int64).clamp(max=gt_keys.shape[1])
+    kk = int(k.max().item())
+    rows_idx = torch.arange(nq, device=ids.device)
+    if X.dtype == torch.uint8:
+        kth = gt_keys.to(torch.int64)[rows_idx, k - 1] & 0xFFFFFFFF
+    else:
+        kth = gt_keys.view(torch.float32)[rows_idx, k - 1].to(torch.float64) * (1 + 1e-6)
+    hits = 0
+    for c0 in range(0, nq, 1024):
+        sl = slice(c0, c0 + 1024)
+        idc = ids[sl, :kk].long()
+        valid = (idc >= 0) & (torch.arange(kk, device=ids.device)[None, :] < k[sl, None])
+        rows = X[idc.clamp(min=0)]
+        if X.dtype == torch.uint8:
+            diff = rows.to(torch.int32) - Q[sl, None, :].to(torch.int32)
+            dist = (diff * diff).sum(-1).to(torch.int64)
+        else:
+            diff = rows.double() - Q[sl, None, :].double()
+            dist = (diff * diff).sum(-1)
+        hits += float((valid & (dist <= kth[sl, None])).sum().item())
+    return hits / float(k.sum().item())
 
 
 def sweep_t90(args, torch, ann, W, log):
@@ -235,15 +260,16 @@ def time_steps(torch, fn, steps, warmup, flush_buf, stream):
 
 
 def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25, 0.5, 0.75, 1.0),
-               plain_qps=1e5):
+               plain_qps=1e5, kq=None, Tq=None):
     """Poisson arrivals of request batches (1-512 queries, log-uniform) into the
     server at fractions of the plain form's measured capacity.  Latency of a
     request = submit to completion as clocked by the server; p50/p99 over
     all requests of a load level."""
     import ctypes
     Qh = W["Qh"]
-    kk = np.full(512, K, np.int32)
-    TT = np.full(512, T, np.int32)
+    kq = np.full(len(Qh), K, np.int32) if kq is None else np.ascontiguousarray(kq, np.int32)
+    Tq = np.full(len(Qh), T, np.int32) if Tq is None else np.ascontiguousarray(Tq, np.int32)
+    kmax = int(kq.max())
     out = []
     for frac in load_fracs:
         rate = frac * plain_qps
@@ -255,7 +281,7 @@ def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25,
         done = {"q": 0, "lat": [], "t_last": 0.0, "stop": False}
 
         def poller():
-            ids = np.empty((512, K), np.int32)
+            ids = np.empty((512, kmax), np.int32)
             while True:
                 with lock:
                     batch = list(outstanding)
@@ -294,6 +320,8 @@ def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25,
             lo = at % (len(Qh) - 512)
             at += n
             q = np.ascontiguousarray(Qh[lo:lo + n])
+            kk = np.ascontiguousarray(kq[lo:lo + n])
+            TT = np.ascontiguousarray(Tq[lo:lo + n])
             tk = ctypes.c_uint64()
             ann.check(ann.lib.ann_serve_submit(srv, q.ctypes.data, n, kk.ctypes.data, TT.ctypes.data,
                                                ctypes.byref(tk)))
@@ -365,9 +393,10 @@ def algorithmic_bytes(stats: np.ndarray, W) -> float:
     outputs; the part dictionaries once per step."""
     spec, info = W["spec"], W["info"]
     d, R, b = spec["d"], spec["R"], spec["b"]
+    es = 1 if spec["dtype"] == "u8" else 4  # bytes per element
     disc, refp, brp, walks, nodes, leaves = (stats[:, i].astype(np.float64) for i in range(6))
-    per_q = disc * d + refp * R * 4 + brp * b * 4 + leaves * 4 + nodes * 0.125 + d + K * 8
-    centers = spec["P"] * spec["n"] * (d // spec["P"])
+    per_q = disc * d * es + refp * R * 4 + brp * b * 4 + leaves * 4 + nodes * 0.125 + d * es + K * 8
+    centers = spec["P"] * spec["n"] * (d // spec["P"]) * es
     return float(per_q.sum() + centers)
 
 
@@ -394,6 +423,8 @@ def main():
     if args.build_only:
         torch.cuda.synchronize()
         return
+    if WORKLOAD != 2:
+        return run_other(args, rank, ws, log, torch, ann, datagen, W)
     T90, rec, table = sweep_t90(args, torch, ann, W, log)
     log(f"T90={T90} recall@10={rec:.4f}")
     nq = W["nq"]
@@ -538,6 +569,88 @@ def main():
             "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
                                                    "bytes_bridges")}, "build_s": W["build_s"]},
         }
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+def run_other(args, rank, ws, log, torch, ann, datagen, W):
+    """Measurement lines for the other workloads (not the headline):
+    3 gist1m: one uneven batch (per-query k in {1,10,100}, T log-uniform in
+      [64, 8192]), persistent vs plain;
+    4 hog4m: recall@10 and queries/s at T in {256, 1024, 4096}, k = 10;
+    5 sift10m: served form with per-request k in {1,10,100}, T in
+      {128, 512, 2048}, against plain and persistent on the same mix."""
+    spec, nq = W["spec"], W["nq"]
+    index, Q = W["index"], W["Q"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stats = torch.zeros((nq, ann.ANN_NSTATS), dtype=torch.int64, device="cuda")
+    if WORKLOAD == 4:
+        kq = np.full(nq, K, np.int32)
+        grid = list(spec["T"])
+    else:
+        kq, Tq = datagen.per_query_params(WORKLOAD, nq)
+        grid = [None]
+    kmax = int(kq.max())
+    kd = torch.from_numpy(kq).cuda()
+    out_ids = torch.empty((nq, kmax), dtype=torch.int32, device="cuda")
+    keyt = torch.int32 if Q.dtype == torch.uint8 else torch.float32
+    out_keys = torch.empty((nq, kmax), dtype=keyt, device="cuda")
+    out_st = torch.empty((nq,), dtype=torch.int32, device="cuda")
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    points = []
+    for Tg in grid:
+        Td = torch.full((nq,), Tg, dtype=torch.int32, device="cuda") if Tg else torch.from_numpy(Tq).cuda()
+
+        def step(mode, st=None):
+            ann.ann_search_batch(index, Q, kd, Td, kmax=kmax, mode=mode, out_ids=out_ids, out_keys=out_keys,
+                                 out_status=out_st, out_stats=st, stream=stream)
+
+        t_plain = time_steps(torch, lambda: step(0), args.steps, args.warmup, flush, stream)
+        t_pers = time_steps(torch, lambda: step(1), args.steps, args.warmup, flush, stream)
+        assert np.all(out_st.cpu().numpy() == 0)
+        rec = recall_at_10(torch, out_ids, W, kd)
+        step(0, stats)
+        torch.cuda.synchronize()
+        st = stats.cpu().numpy()
+        alg = algorithmic_bytes(st, W)
+        k_ms = statistics.mean(t_plain)
+        pt = {"T": Tg if Tg else "per query", "recall": rec,
+              "plain_qps": nq * args.steps / (sum(t_plain) / 1e3),
+              "persistent_qps": nq * args.steps / (sum(t_pers) / 1e3),
+              "persistent_ms_per_step": statistics.mean(t_pers),
+              "roofline": {"bound": "hbm", "achieved": alg / (k_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                           "frac": alg / (k_ms / 1e3) / 1e9 / peak, "traffic": None,
+                           "algorithmic_bytes_per_launch": alg},
+              "search_stats_mean_per_query": {n: float(st[:, i].mean()) for i, n in enumerate(ann.STAT_NAMES)}}
+        log(f"T={pt['T']}: recall {rec:.4f}, plain {pt['plain_qps']:.0f} q/s, persistent {pt['persistent_qps']:.0f} q/s")
+        points.append(pt)
+    # headline point: the first budget reaching recall 0.9 (else the last)
+    head = next((p for p in points if p["recall"] >= 0.9), points[-1])
+    served = None
+    if WORKLOAD == 5 and not args.no_serve:
+        served = served_run(torch, ann, W, 0, datagen, log, plain_qps=head["plain_qps"], kq=kq, Tq=Tq)
+    clocks = None
+    if rank == 0:
+        names = {3: "gist1m: N=%d x 384 float32, %d queries, per-query k in {1,10,100} and T log-uniform in "
+                    "[64, 8192], R=20, P=3 x n=128, b<=5, t=100",
+                 4: "hog4m: N=%d x 512 float32, %d queries, k=10, T in {256,1024,4096}, R=16, P=4 x n=256, b<=5, "
+                    "t=100",
+                 5: "sift10m: N=%d x 128 uint8, %d queries, per-query k in {1,10,100} and T in {128,512,2048}, "
+                    "R=16, P=4 x n=256, b<=5, t=100"}
+        line = {"metric": METRIC, "value": head["persistent_qps"], "unit": "queries/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["persistent_ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u8" if Q.dtype == torch.uint8 else "f32",
+                "data": "synthetic (seeded mixture shaped like the paper's workload; the datasets are not available)",
+                "config": {"workload": names[WORKLOAD] % (W["N"], nq), "mode": "persistent (CUDA graph)",
+                           "l2": "flushed before every timed step (256 MB write)",
+                           "recall": "mean r/k over queries, k capped at 32 for the ground truth"},
+                "points": points, "served": served, "clocks": clocks, "gpu_launches": None,
+                "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
+                                                       "bytes_bridges")}, "build_s": W["build_s"]}}
         print(json.dumps(line), flush=True)
     barrier(ws)
 
