@@ -142,6 +142,8 @@ typedef struct {
     int64_t bridged_refs;     /* distinct references attached to some bridge */
     double alpha;             /* bridged_refs / n^P */
     int64_t bytes_vectors, bytes_graph, bytes_bridges;
+    int64_t groups;   /* c2 groups of the prefix index (0: no group level; built for P = 4 when the
+                         bridges average >= 32 per prefix node) */
 } ann_index_info;
 int ann_index_get_info(const ann_index *index, ann_index_info *out);
 

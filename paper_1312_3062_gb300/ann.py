@@ -41,7 +41,7 @@ class ann_index_desc(ctypes.Structure):
 class ann_index_info(ctypes.Structure):
     _fields_ = [("N", i64), ("M", i64), ("d", i32), ("R", i32), ("P", i32), ("n", i32), ("b", i32),
                 ("dtype", i32), ("bridged_refs", i64), ("alpha", f64), ("bytes_vectors", i64),
-                ("bytes_graph", i64), ("bytes_bridges", i64)]
+                ("bytes_graph", i64), ("bytes_bridges", i64), ("groups", i64)]
 
 
 def _sig(name, argtypes, restype=ctypes.c_int):

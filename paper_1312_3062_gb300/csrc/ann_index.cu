@@ -280,6 +280,42 @@ __global__ void bg_bits_kernel(const uint32_t *offA, int64_t nA, uint32_t *bmA) 
     bmA[w] = v;
 }
 
+// groups of bridges sharing (prefix node, c2): flag the first of each
+__global__ void bg_gflag_kernel(const uint32_t *ubid, int64_t M, uint32_t n, uint32_t *flag) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    flag[j] = (j == 0 || ubid[j] / n != ubid[j - 1] / n) ? 1u : 0u;
+}
+
+__global__ void bg_gscatter_kernel(const uint32_t *ubid, const uint32_t *flag, const uint32_t *gincl, int64_t M,
+                                   uint32_t n, uint32_t *gstart, uint8_t *gc2) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > M) return;
+    if (j == M) {
+        gstart[M > 0 ? gincl[M - 1] : 0] = (uint32_t)M;
+        return;
+    }
+    if (flag[j]) {
+        const uint32_t g = gincl[j] - 1;
+        gstart[g] = (uint32_t)j;
+        gc2[g] = (uint8_t)((ubid[j] / n) % n);
+    }
+}
+
+// goff[a] = first group whose prefix node is >= a  (a in [0, nA])
+__global__ void bg_goff_kernel(const uint32_t *ubid, const uint32_t *gstart, int64_t G, uint32_t suf, int64_t nA,
+                               uint32_t *goff) {
+    int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (a > nA) return;
+    int64_t lo = 0, hi = G;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)(ubid[gstart[mid]] / suf) < a) lo = mid + 1;
+        else hi = mid;
+    }
+    goff[a] = (uint32_t)lo;
+}
+
 __global__ void mark_refs_kernel(const int32_t *brefs, int64_t total, uint8_t *mark) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= total) return;
@@ -323,13 +359,46 @@ static int finish_bridge_index(ann_index *ix, DBuf<uint32_t> &ubid, int64_t M, c
     bg_offa_kernel<<<nblk(dv.nA + 1), 256, 0, s>>>(ubid.p, M, suf, dv.nA, offA.p);
     bg_bits_kernel<<<nblk((dv.nA + 31) / 32), 256, 0, s>>>(offA.p, dv.nA, bmA.p);
     ANN_CUDA(cudaGetLastError());
+    // c2 groups inside each prefix node: two suffix parts, and on average at
+    // least 32 bridges per prefix node (otherwise reading the leaves is cheaper)
+    int64_t G = 0;
+    DBuf<uint32_t> goff, gstart;
+    DBuf<uint8_t> gc2;
+    if (dv.P - dv.PA == 2 && M >= 32 * dv.nA) {
+        DBuf<uint32_t> flag, gincl;
+        ANN_CUDA_ALLOC(flag, M);
+        ANN_CUDA_ALLOC(gincl, M);
+        bg_gflag_kernel<<<nblk(M), 256, 0, s>>>(ubid.p, M, (uint32_t)dv.n, flag.p);
+        size_t tb = 0;
+        ANN_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, flag.p, gincl.p, M, s));
+        DBuf<uint8_t> temp;
+        ANN_CUDA_ALLOC(temp, tb);
+        ANN_CUDA(cub::DeviceScan::InclusiveSum(temp.p, tb, flag.p, gincl.p, M, s));
+        uint32_t g32 = 0;
+        ANN_CUDA(cudaMemcpyAsync(&g32, gincl.p + (M - 1), 4, cudaMemcpyDeviceToHost, s));
+        ANN_CUDA(cudaStreamSynchronize(s));
+        G = g32;
+        ANN_CUDA_ALLOC(gstart, G + 1);
+        ANN_CUDA_ALLOC(gc2, G);
+        ANN_CUDA_ALLOC(goff, dv.nA + 1);
+        bg_gscatter_kernel<<<nblk(M + 1), 256, 0, s>>>(ubid.p, flag.p, gincl.p, M, (uint32_t)dv.n, gstart.p, gc2.p);
+        bg_goff_kernel<<<nblk(dv.nA + 1), 256, 0, s>>>(ubid.p, gstart.p, G, suf, dv.nA, goff.p);
+        ANN_CUDA(cudaGetLastError());
+    }
     ANN_CUDA(cudaStreamSynchronize(s));
     ix->leaf = leaf.release();
     ix->offA = offA.release();
     ix->bmA = bmA.release();
+    ix->goff = goff.release();
+    ix->gstart = gstart.release();
+    ix->gc2 = gc2.release();
     dv.leaf = ix->leaf;
     dv.offA = ix->offA;
     dv.bmA = ix->bmA;
+    dv.ngroups = G;
+    dv.goff = ix->goff;
+    dv.gstart = ix->gstart;
+    dv.gc2 = ix->gc2;
     dv.M = M;
     return count_bridged(ix, s);
 }
@@ -481,6 +550,9 @@ static void destroy(ann_index *ix) {
     cudaFree(ix->offA);
     cudaFree(ix->leaf);
     cudaFree(ix->brefs);
+    cudaFree(ix->goff);
+    cudaFree(ix->gstart);
+    cudaFree(ix->gc2);
     delete ix;
 }
 
@@ -640,7 +712,9 @@ extern "C" int ann_index_get_info(const ann_index *index, ann_index_info *out) {
     const size_t es = dv.dtype == ANN_U8 ? 1 : 4;
     out->bytes_vectors = (int64_t)(dv.N * dv.d * es);
     out->bytes_graph = dv.N * dv.R * 4;
-    out->bytes_bridges = dv.M * (4 + 4 * dv.b) + (dv.nA + 1) * 4 + (dv.nA + 31) / 32 * 4;
+    out->bytes_bridges = dv.M * (4 + 4 * dv.b) + (dv.nA + 1) * 4 + (dv.nA + 31) / 32 * 4 +
+                         (dv.ngroups ? (dv.ngroups + 1) * 4 + dv.ngroups + (dv.nA + 1) * 4 : 0);
+    out->groups = dv.ngroups;
     return ANN_OK;
 }
 

@@ -43,7 +43,11 @@ constexpr int kMaxT = 8192;
 // (PA = min(2, P-1)) form the prefix "A" node a = c0*n + c1 (or c0), the
 // remaining parts the suffix, packed as mixed radix `leaf`.  For every prefix
 // node: a presence bit (bmA) and a CSR range [offA[a], offA[a+1]) of
-// bridges; each bridge has b reference slots (-1 padded).
+// bridges; each bridge has b reference slots (-1 padded).  With two suffix
+// parts (P = 4) and many bridges per prefix node, the bridges of a node are
+// also grouped by their third center c2: groups [goff[a], goff[a+1]), group g
+// holds c2 = gc2[g] and the bridges [gstart[g], gstart[g+1]), so a walk can
+// bound a whole group by D0 + D1 + D2[c2] + min D3 before reading its leaves.
 struct DevIndex {
     int dtype;
     int64_t N;
@@ -58,6 +62,10 @@ struct DevIndex {
     const uint32_t *offA;// nA+1
     const uint32_t *leaf;// M
     const int32_t *brefs;// M*b
+    int64_t ngroups;        // c2 groups (0: no group level)
+    const uint32_t *goff;   // nA+1
+    const uint32_t *gstart; // ngroups+1
+    const uint8_t *gc2;     // ngroups
 };
 
 }  // namespace ann
@@ -70,6 +78,8 @@ struct ann_index {
     int32_t *G;
     uint32_t *bmA, *offA, *leaf;
     int32_t *brefs;
+    uint32_t *goff, *gstart;
+    uint8_t *gc2;
     int64_t bridged_refs;
     // cached persistent-mode plans (see ann_search.cu)
     void *plans;
@@ -85,6 +95,7 @@ int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, co
 // implemented in ann_knn_tc.cu: exact k-NN of uint8 rows on the tensor cores, d in {64, 128}, k <= 32
 int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_t nq, int d, int k,
                   int exclude_self, int32_t *out_ids, uint32_t *out_keys, cudaStream_t s);
+bool knn_u8_tensor_fits(int d, int k);
 // implemented in ann_index.cu
 int build_bridge_index_from_host(ann_index *ix, int64_t M, const uint64_t *ids,
                                  const int64_t *offsets, const int32_t *refs);

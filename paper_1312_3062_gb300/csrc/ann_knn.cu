@@ -234,7 +234,7 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
     ANN_ARG(!exclude_self || (queries == refs && nq == N), "exclude_self needs queries == refs");
     if (nq == 0) return ANN_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    if (dtype == ANN_U8 && (d == 64 || d == 128))
+    if (dtype == ANN_U8 && (d == 64 || d == 128) && knn_u8_tensor_fits(d, k))
         return knn_u8_tensor((const uint8_t *)refs, N, (const uint8_t *)queries, nq, d, k, exclude_self, out_ids,
                              (uint32_t *)out_keys, s);
     // float32 at scale: candidates from tensor-core dot products, exact keys

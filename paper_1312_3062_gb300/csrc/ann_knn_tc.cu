@@ -453,6 +453,14 @@ size_t smem_bytes(int d, int k) {
 
 }  // namespace tc
 
+// Whether the tensor-core kernel's shared memory for (d, k) fits a CTA.
+bool knn_u8_tensor_fits(int d, int k) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    return tc::smem_bytes(d, k) <= (size_t)optin;
+}
+
 // Exact k-NN of uint8 rows on the tensor cores.  Requires d in {64, 128}.
 int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_t nq, int d, int k,
                   int exclude_self, int32_t *out_ids, uint32_t *out_keys, cudaStream_t s) {

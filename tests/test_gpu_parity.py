@@ -203,6 +203,15 @@ def test_search_mixed_budgets_matches_oracle(ann, dtype, P, n, R, d):
         np.testing.assert_array_equal(gi, wi)
         assert_keys(gk, wk, dtype)
         np.testing.assert_array_equal(gst[:, 0], wst["discovered"])
+    if P == 4:
+        # the c2 group level exists exactly when the bridges average >= 32 per
+        # prefix node (c0, c1); the n = 8 case has it, so its walks ran over it
+        ix = ann.Index.create(dev(X), dev(G), dev(C), t=100, b=5, bridges=bg)
+        info = ix.info()
+        assert (info["groups"] > 0) == (info["M"] >= 32 * n * n)
+        if n == 8:
+            assert info["groups"] > 0
+        ix.free()
 
 
 def test_search_edge_cases(ann, tiny_sift):
