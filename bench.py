@@ -401,6 +401,16 @@ def algorithmic_bytes(stats: np.ndarray, W) -> float:
     return float(per_q.sum() + centers)
 
 
+def search_kernel_digest() -> str:
+    """sha256 over the search kernel's device sources (the DRAM traffic in
+    profiles/ is valid only for the kernel it was measured on)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("ann_search_dev.cuh", "ann_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1312_3062_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def main():
     args = parse()
     rank, ws, local = dist_init(args)
@@ -478,8 +488,7 @@ def main():
     if os.path.exists(prof):
         import hashlib
         pj = json.load(open(prof))
-        src = os.path.join(ROOT, "paper_1312_3062_gb300", "csrc", "ann_search.cu")
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        digest = search_kernel_digest()
         if (pj.get("T") == T90 and pj.get("nq") == nq and pj.get("N") == W["N"]
                 and pj.get("kernel_source_sha256") == digest):
             traffic = pj.get("dram_bytes_per_launch")
@@ -566,7 +575,7 @@ def main():
             "search_stats_mean_per_query": search_stats,
             "cpu_baseline": cpu_baseline,
             "clocks": clocks,
-            "gpu_launches": args.steps * 2,
+            "gpu_launches": args.steps,  # uniform budget: one search kernel per replayed graph
             "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
                                                    "bytes_bridges")}, "build_s": W["build_s"]},
         }

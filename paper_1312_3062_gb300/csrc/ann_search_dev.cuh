@@ -1069,7 +1069,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     ws.kmaxall = kmaxall;
     ws.msuf = msuf;
     if (DT == ANN_U8) {
-        uint32_t w = kmin >> 6;
+        uint32_t w = kmin >> 8;  // measured on the SIFT-shaped 1M index: narrow first windows walk fewest leaves
         ws.width = w < 1 ? 1 : w;
     } else {
         ws.width = 1u << 16;  // about 0.8% relative in float32 bit space
