@@ -45,7 +45,8 @@ static const int kWindowedFromT = 1024;
 struct Tune {
     int warps;
     int bcap;
-    bool stage;  // stage the next pop's neighbour vectors (cp.async)
+    bool stage;         // stage the next pop's neighbour vectors (cp.async)
+    bool tickets = true;  // persistent form: pull queries from a ticket (else a fixed grid-stride share)
 };
 
 // Warps per CTA: the count that keeps the most warps resident per SM given
@@ -85,11 +86,19 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
 }
 
 
+// The dynamic shared-memory limit of a kernel is a property of the function,
+// read again whenever a launch (or a graph node) is checked, so it is raised
+// once to the device's opt-in maximum rather than set per launch: a captured
+// graph may hold nodes of one kernel with different sizes.
 template <int DT, bool WIN>
 static cudaError_t config_kernel(size_t smem, int threads, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, WIN, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    static bool raised = false;
+    if (!raised) {
+        cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, WIN, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g_smem_optin);
+        if (e != cudaSuccess) return e;
+        raised = true;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<DT, WIN, false>, threads, smem);
 }
 
@@ -115,7 +124,7 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
-    A.ticket = ticket;
+    A.ticket = (persistent && tn.tickets) ? ticket : nullptr;
     const bool win = capT >= kWindowedFromT;
     uint32_t gcap = (uint32_t)(2 * capT);
     if (gcap > 8192) gcap = 8192;
@@ -136,7 +145,10 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     if (e != cudaSuccess) return cuda_fail(e, "search kernel configuration");
     if (blocks_per_sm < 1) blocks_per_sm = 1;
     const int64_t cap = (int64_t)g_num_sms * blocks_per_sm;
-    int64_t want = (persistent || list_count) ? cap : (list_len + tn.warps - 1) / tn.warps;
+    // ticket queue: one wave; fixed shares: up to four waves, sized by the
+    // query count when it is known on the host
+    const bool by_ticket = persistent && ticket && tn.tickets;
+    int64_t want = by_ticket ? cap : (list_count ? cap * 4 : (list_len + tn.warps - 1) / tn.warps);
     // plain launches grid-stride beyond four waves; windowed ones beyond one wave (bounded scratch)
     const int64_t lim = win ? cap : cap * 4;
     if (want > lim) want = lim;
@@ -334,8 +346,9 @@ static std::vector<Tune> tune_candidates(const DevIndex &ix, int capT, int kmax)
     const Tune d = choose_tune(ix, capT, kmax);
     std::vector<Tune> c{d};
     for (int w : {1, 2, 3, 4})
-        if (w < d.warps) c.push_back(Tune{w, d.bcap, true});
-    c.push_back(Tune{d.warps, d.bcap, false});
+        if (w < d.warps) c.push_back(Tune{w, d.bcap, true, true});
+    c.push_back(Tune{d.warps, d.bcap, false, true});
+    c.push_back(Tune{d.warps, d.bcap, true, false});  // the plain form's fixed grid-stride shares
     return c;
 }
 

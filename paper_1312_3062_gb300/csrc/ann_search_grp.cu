@@ -6,11 +6,20 @@
 
 namespace ann {
 
+// the function's dynamic shared-memory limit is raised once to the opt-in
+// maximum (a captured graph may hold nodes of one kernel with different sizes)
 template <int DT, bool WIN>
 static cudaError_t config_one(size_t smem, int threads, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, WIN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+    static bool raised = false;
+    if (!raised) {
+        int dev = 0, optin = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(search_kernel<DT, WIN, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+        if (e != cudaSuccess) return e;
+        raised = true;
+    }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<DT, WIN, true>, threads, smem);
 }
 
