@@ -356,18 +356,15 @@ def oracle_sample_qps(torch, ann, W, T, budget_s=12.0):
     bg = host_bridges(W["index"])
     X, G, C, Qh = W["Xh"], W["G_host"], W["C_host"], W["Qh"]
     cores = os.cpu_count() or 1
+    oracle.search(X, G, C, bg, Qh[:cores], K, T, kmax=K, nthreads=cores)  # warm the caches
+    passes, done = 0, 0
     t0 = time.perf_counter()
-    oracle.search(X, G, C, bg, Qh[:cores], K, T, kmax=K, nthreads=cores)
-    per_q = (time.perf_counter() - t0) / cores
-    if per_q * len(Qh) >= budget_s:
-        n, passes = int(max(cores, budget_s / max(per_q, 1e-9))), 1
-    else:
-        n, passes = len(Qh), int(max(1, round(budget_s / (per_q * len(Qh)))))
-    t0 = time.perf_counter()
-    for _ in range(passes):
-        oracle.search(X, G, C, bg, Qh[:n], K, T, kmax=K, nthreads=cores)
+    while time.perf_counter() - t0 < budget_s and passes < 1000:
+        oracle.search(X, G, C, bg, Qh, K, T, kmax=K, nthreads=cores)
+        passes += 1
+        done += len(Qh)
     el = time.perf_counter() - t0
-    return n * passes / el, cores, n, passes, el
+    return done / el, cores, len(Qh), passes, el
 
 
 def host_bridges(index):
