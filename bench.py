@@ -262,83 +262,39 @@ def time_steps(torch, fn, steps, warmup, flush_buf, stream):
     return times
 
 
-def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25, 0.5, 0.75, 1.0),
+def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25, 0.5, 0.75, 1.0, 1.25),
                plain_qps=1e5, kq=None, Tq=None):
     """Poisson arrivals of request batches (1-512 queries, log-uniform) into the
-    server at fractions of the plain form's measured capacity.  Latency of a
-    request = submit to completion as clocked by the server; p50/p99 over
-    all requests of a load level."""
+    server at fractions of the plain form's measured capacity, replayed by the
+    library's native load driver (ann_serve_replay).  Latency of a request =
+    submit to completion as clocked by the server; p50/p99 over all requests
+    of a load level; throughput = queries / (first arrival to last completion)."""
     import ctypes
-    Qh = W["Qh"]
+    Qh = np.ascontiguousarray(W["Qh"])
     kq = np.full(len(Qh), K, np.int32) if kq is None else np.ascontiguousarray(kq, np.int32)
     Tq = np.full(len(Qh), T, np.int32) if Tq is None else np.ascontiguousarray(Tq, np.int32)
-    kmax = int(kq.max())
     out = []
     for frac in load_fracs:
         rate = frac * plain_qps
-        arrivals, sizes = datagen.poisson_requests(WORKLOAD, 200000, rate_qps=rate)
+        arrivals, sizes = datagen.poisson_requests(WORKLOAD, 400000, rate_qps=rate)
+        n = int(np.searchsorted(arrivals, duration_s))
+        arrivals = np.ascontiguousarray(arrivals[:n], np.float64)
+        sizes = np.ascontiguousarray(sizes[:n], np.int32)
+        ends = np.cumsum(sizes.astype(np.int64))
+        first = np.ascontiguousarray((ends - sizes) % (len(Qh) - 512), np.int64)
+        lat = np.zeros(n, np.float64)
+        el = ctypes.c_double()
         srv = ctypes.c_void_p()
         ann.check(ann.lib.ann_server_create(W["index"].handle, 512 << 20, 4, ctypes.byref(srv)))
-        outstanding = []
-        lock = threading.Lock()
-        done = {"q": 0, "lat": [], "t_last": 0.0, "stop": False}
-
-        def poller():
-            ids = np.empty((512, kmax), np.int32)
-            while True:
-                with lock:
-                    batch = list(outstanding)
-                    stop = done["stop"]
-                if stop and not batch:
-                    return
-                keep = []
-                for tk, n in batch:
-                    rc = ann.lib.ann_serve_poll(srv, tk, ids.ctypes.data, None, None)
-                    if rc == ann.ANN_OK:
-                        done["q"] += n
-                        done["lat"].append(ann.lib.ann_serve_latency(srv, tk) * 1e3)
-                        done["t_last"] = time.perf_counter()
-                    elif rc == ann.ANN_PENDING:
-                        keep.append((tk, n))
-                    else:
-                        ann.check(rc)
-                with lock:
-                    gone = set(batch) - set(keep)
-                    outstanding[:] = [x for x in outstanding if x not in gone]
-                time.sleep(0.0001)
-
-        th = threading.Thread(target=poller, daemon=True)
-        th.start()
-        t0 = time.perf_counter()
-        at = 0
-        nsub = 0
-        for i in range(len(sizes)):
-            now = time.perf_counter() - t0
-            if arrivals[i] > duration_s:
-                break
-            wait = arrivals[i] - now
-            if wait > 0:
-                time.sleep(wait)
-            n = int(sizes[i])
-            lo = at % (len(Qh) - 512)
-            at += n
-            q = np.ascontiguousarray(Qh[lo:lo + n])
-            kk = np.ascontiguousarray(kq[lo:lo + n])
-            TT = np.ascontiguousarray(Tq[lo:lo + n])
-            tk = ctypes.c_uint64()
-            ann.check(ann.lib.ann_serve_submit(srv, q.ctypes.data, n, kk.ctypes.data, TT.ctypes.data,
-                                               ctypes.byref(tk)))
-            with lock:
-                outstanding.append((tk.value, n))
-            nsub += 1
-        with lock:
-            done["stop"] = True
-        th.join()
-        ann.lib.ann_server_destroy(srv)
-        span = done["t_last"] - t0
-        lat = np.asarray(done["lat"])
-        rec = {"offered_qps": rate, "load_frac": frac, "qps": done["q"] / span, "requests": nsub,
-               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+        try:
+            ann.check(ann.lib.ann_serve_replay(srv, Qh.ctypes.data, kq.ctypes.data, Tq.ctypes.data, n,
+                                               first.ctypes.data, sizes.ctypes.data, arrivals.ctypes.data,
+                                               lat.ctypes.data, ctypes.byref(el)))
+        finally:
+            ann.lib.ann_server_destroy(srv)
+        lat_ms = lat * 1e3
+        rec = {"offered_qps": rate, "load_frac": frac, "qps": float(sizes.sum()) / el.value, "requests": n,
+               "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99))}
         log(f"served at {frac:.2f} x plain: {rec['qps']:.0f} q/s, p50 {rec['p50_ms']:.2f} ms, "
             f"p99 {rec['p99_ms']:.2f} ms")
         out.append(rec)

@@ -216,6 +216,21 @@ int ann_serve_poll(ann_server *server, uint64_t ticket, int32_t *host_ids, void 
  * request, measured by the server; -1 if unknown. */
 double ann_serve_latency(ann_server *server, uint64_t ticket);
 
+/* Load replay, a measurement tool with no counterpart in the paper.  Submits
+ * nreq requests to the server from the calling thread, request r at
+ * arrival_s[r] seconds after the call (non-decreasing), holding the size[r]
+ * query rows starting at row first[r] of host_queries (host memory, the
+ * index's dtype and d) with per-query k and T taken from the same rows of the
+ * host arrays k and T; a second native thread collects every ticket (results
+ * are discarded).  Writes each request's latency (submit -> completion,
+ * seconds) to out_latency_s[nreq] and the time from the first arrival to the
+ * last completion to *out_elapsed_s.  Returns ANN_OK or the first error of a
+ * submission or a poll; all requests already submitted are collected before
+ * it returns. */
+int ann_serve_replay(ann_server *server, const void *host_queries, const int32_t *k, const int32_t *T,
+                     int32_t nreq, const int64_t *first, const int32_t *size, const double *arrival_s,
+                     double *out_latency_s, double *out_elapsed_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,11 +68,12 @@ _sig("ann_server_destroy", [P_])
 _sig("ann_serve_submit", [P_, P_, i32, P_, P_, ctypes.POINTER(u64)])
 _sig("ann_serve_poll", [P_, u64, P_, P_, P_])
 _sig("ann_serve_latency", [P_, u64], f64)
+_sig("ann_serve_replay", [P_, P_, P_, P_, i32, P_, P_, P_, P_, P_])
 
 EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_train_centers", "ann_index_create",
             "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges",
             "ann_search_batch", "ann_server_create", "ann_server_destroy", "ann_serve_submit", "ann_serve_poll",
-            "ann_serve_latency")
+            "ann_serve_latency", "ann_serve_replay")
 
 
 class AnnError(RuntimeError):

@@ -389,3 +389,78 @@ extern "C" double ann_serve_latency(ann_server *S, uint64_t ticket) {
     auto it = S->done_latency.find(ticket);
     return it == S->done_latency.end() ? -1.0 : it->second;
 }
+
+// Load replay (a measurement tool; the paper has no counterpart): requests are
+// submitted from the calling thread at their arrival times and collected by a
+// second native thread, so the measured rate and latencies are the server's,
+// not those of a scripting-language driver.
+extern "C" int ann_serve_replay(ann_server *S, const void *host_queries, const int32_t *k, const int32_t *T,
+                                int32_t nreq, const int64_t *first, const int32_t *size, const double *arrival_s,
+                                double *out_latency_s, double *out_elapsed_s) {
+    ANN_ARG(S && host_queries && k && T && first && size && arrival_s && out_latency_s && out_elapsed_s,
+            "all arguments are required");
+    ANN_ARG(nreq >= 1, "nreq must be >= 1");
+    for (int32_t r = 0; r < nreq; r++) {
+        ANN_ARG(size[r] >= 1 && size[r] <= kServeMaxBatch && first[r] >= 0, "request size or offset out of range");
+        ANN_ARG(r == 0 || arrival_s[r] >= arrival_s[r - 1], "arrival times must not decrease");
+    }
+    const size_t vb = S->vbytes;
+    std::vector<uint64_t> tickets((size_t)nreq, 0);
+    std::atomic<int32_t> submitted{0};
+    std::atomic<bool> failed{false}, submit_done{false};
+    std::atomic<int> poll_error{ANN_OK};
+    const auto t0 = Clock::now();
+    Clock::time_point t_last = t0;
+    std::thread collector([&] {
+        std::vector<int32_t> ids((size_t)kServeMaxBatch * kMaxK);
+        std::vector<int32_t> pending;
+        int32_t seen = 0, done = 0;
+        // until every submitted request is collected (or a poll fails)
+        while (poll_error.load() == ANN_OK) {
+            const bool last = submit_done.load(std::memory_order_acquire);
+            const int32_t ns = submitted.load(std::memory_order_acquire);
+            if (last && done == ns) break;
+            while (seen < ns) pending.push_back(seen++);
+            for (size_t i = 0; i < pending.size();) {
+                const int32_t r = pending[i];
+                const int rc = ann_serve_poll(S, tickets[(size_t)r], ids.data(), nullptr, nullptr);
+                if (rc == ANN_OK) {
+                    out_latency_s[r] = ann_serve_latency(S, tickets[(size_t)r]);
+                    t_last = Clock::now();
+                    done++;
+                    pending[i] = pending.back();
+                    pending.pop_back();
+                } else if (rc == ANN_PENDING) {
+                    i++;
+                } else {
+                    poll_error.store(rc);
+                    failed.store(true);
+                    break;
+                }
+            }
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    });
+    int rc = ANN_OK;
+    for (int32_t r = 0; r < nreq && !failed.load(); r++) {
+        const auto at = t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double>(arrival_s[r]));
+        for (auto now = Clock::now(); now < at; now = Clock::now()) {
+            if (at - now > std::chrono::microseconds(300))
+                std::this_thread::sleep_for(at - now - std::chrono::microseconds(200));
+        }
+        uint64_t tk = 0;
+        rc = ann_serve_submit(S, (const uint8_t *)host_queries + (size_t)first[r] * vb, size[r], k + first[r],
+                              T + first[r], &tk);
+        if (rc != ANN_OK) {
+            failed.store(true);
+            break;
+        }
+        tickets[(size_t)r] = tk;
+        submitted.store(r + 1, std::memory_order_release);
+    }
+    submit_done.store(true, std::memory_order_release);
+    collector.join();
+    if (rc == ANN_OK) rc = poll_error.load();
+    *out_elapsed_s = std::chrono::duration<double>(t_last - t0).count() - arrival_s[0];
+    return rc;
+}

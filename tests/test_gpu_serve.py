@@ -135,3 +135,25 @@ def test_batch_matches_oracle(setup):
     np.testing.assert_array_equal(ids_ref[sel], wi)
     np.testing.assert_array_equal(keys_ref[sel].view(np.uint32).astype(np.float64),
                                   np.where(np.isinf(wk), 4294967295.0, wk))
+
+
+def test_native_replay_collects_every_request(setup):
+    # the load driver submits at the given arrival times and collects every
+    # ticket; the server then holds no live request and every latency is set
+    ann, ix, X, Q, k, T, ids_ref, keys_ref, *_ = setup
+    srv = ctypes.c_void_p()
+    ann.check(ann.lib.ann_server_create(ix.handle, 64 << 20, 3, ctypes.byref(srv)))
+    rng = np.random.default_rng(11)
+    n = 60
+    sizes = rng.integers(1, 40, n).astype(np.int32)
+    first = rng.integers(0, len(Q) - 40, n).astype(np.int64)
+    arrivals = np.cumsum(rng.exponential(0.0005, n)).astype(np.float64)
+    lat = np.zeros(n, np.float64)
+    el = ctypes.c_double()
+    q = np.ascontiguousarray(Q)
+    ann.check(ann.lib.ann_serve_replay(srv, q.ctypes.data, k.ctypes.data, T.ctypes.data, n, first.ctypes.data,
+                                       sizes.ctypes.data, arrivals.ctypes.data, lat.ctypes.data, ctypes.byref(el)))
+    assert np.all(lat > 0) and el.value > 0
+    # a ticket that was collected is gone
+    assert ann.lib.ann_serve_poll(srv, 1, np.empty((40, 100), np.int32).ctypes.data, None, None) == ann.ANN_ERR_ARG
+    ann.lib.ann_server_destroy(srv)
