@@ -151,6 +151,13 @@ int ann_index_get_info(const ann_index *index, ann_index_info *out);
  * and refs (int32[M*b], each list padded with -1). */
 int ann_index_get_bridges(const ann_index *index, uint64_t *ids, int32_t *refs);
 
+/* Reference lists of selected bridge ids (host arrays): refs (int32[nids*b])
+ * receives each id's list (Sec. 4.1), ascending by (key to the bridge, id),
+ * padded with -1; an id without references gets an all -1 row.  Reads only
+ * the prefix offsets and the selected nodes' leaves, for indexes too large to
+ * copy back whole.  ANN_ERR_ARG for an id >= n^P. */
+int ann_index_lookup_bridges(const ann_index *index, const uint64_t *ids, int64_t nids, int32_t *refs);
+
 /* ------------------------------------------------------------------------ */
 /* Search: Algorithm 1 (Sec. 4.2)                                            */
 /* ------------------------------------------------------------------------ */

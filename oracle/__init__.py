@@ -63,6 +63,8 @@ def _load():
             lib.oracle_multiseq.restype = i64
             lib.oracle_bridge_graph.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, P, P, P, i32]
             lib.oracle_bridge_graph.restype = i64
+            lib.oracle_bridge_lists.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, i64, P, P, P, i32]
+            lib.oracle_bridge_lists.restype = None
             lib.oracle_search.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P, P, P,
                                           i64, P, P, i32, P, P, P, P, i32, i32]
             lib.oracle_search.restype = i32
@@ -164,6 +166,30 @@ def bridge_graph(X: np.ndarray, centers: np.ndarray, t: int, b: int, nthreads: i
     nnz = int(offsets[M])
     return {"bridges": bridges[:M].copy(), "offsets": offsets[:M + 1].copy(),
             "refs": refs[:nnz].copy(), "keys": keys[:nnz].copy(), "P": P, "n": n}
+
+
+def bridge_lists(X: np.ndarray, centers: np.ndarray, t: int, b: int, sel: np.ndarray, nthreads: int = 0):
+    """The bridge graph's reference lists of the selected bridge ids only (same
+    definition as bridge_graph, without sorting all N*t triples).  sel: strictly
+    ascending bridge ids.  Returns (counts (nsel,), refs (nsel, b) -1 padded,
+    keys (nsel, b) +inf padded)."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    centers = np.ascontiguousarray(centers)
+    assert centers.dtype == X.dtype
+    sel = np.ascontiguousarray(sel, dtype=np.uint64)
+    assert np.all(np.diff(sel.astype(np.float64)) > 0)
+    P, n, dp = centers.shape
+    N, d = X.shape
+    counts = np.empty(len(sel), np.int32)
+    refs = np.full((len(sel), b), -1, np.int32)
+    keys = np.full((len(sel), b), np.inf, np.float64)
+    lib.oracle_bridge_lists(_ptr(X), N, d, _dtype_code(X), P, n, _ptr(centers), t, b, _ptr(sel), len(sel),
+                            _ptr(counts), _ptr(refs), _ptr(keys), _threads(nthreads))
+    for i, c in enumerate(counts):
+        refs[i, c:] = -1
+        keys[i, c:] = np.inf
+    return counts, refs, keys
 
 
 def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, queries: np.ndarray,

@@ -607,6 +607,81 @@ int64_t oracle_bridge_graph(const void *X, int64_t N, int d, int dtype, int P, i
     return M;
 }
 
+/* Bridge lists of selected bridges only (Sec. 4.1, the same definition as
+   oracle_bridge_graph, restricted to the ids in sel): every reference's top-t
+   bridges are enumerated as above; a selected bridge keeps the b smallest
+   (key, ref id) among the references that chose it.  For indexes whose full
+   list of N*t triples is too large to sort in a test.
+   sel: nsel strictly ascending bridge ids.  Outputs: counts[nsel] and, per
+   selected bridge i, refs/keys[i*b .. i*b + counts[i]) ascending. */
+typedef struct {
+    const void *X, *centers;
+    int64_t N;
+    int d, dtype, P, n, t, b;
+    const uint64_t *sel;
+    int64_t nsel;
+    int32_t *counts, *refs; /* shared result, guarded by mu */
+    double *keys;
+    int64_t next;
+    pthread_mutex_t mu;
+} bl_job_t;
+
+static int64_t sel_find(const uint64_t *sel, int64_t nsel, uint64_t id) {
+    int64_t lo = 0, hi = nsel;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (sel[mid] < id) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < nsel && sel[lo] == id ? lo : -1;
+}
+
+static void *bl_worker(void *arg) {
+    bl_job_t *j = (bl_job_t *)arg;
+    tables_t tb = tables_alloc(j->P, j->n);
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t i = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (i >= j->N) break;
+        tables_build(&tb, row_ptr(j->X, i, j->d, j->dtype), j->d, j->dtype, j->P, j->n, j->centers);
+        mseq_t ms;
+        ms_init(&ms, &tb);
+        ms_item it;
+        for (int s = 0; s < j->t && ms_next(&ms, &it); s++) {
+            int64_t w = sel_find(j->sel, j->nsel, bridge_id_of(&tb, it.r));
+            if (w < 0) continue;
+            pthread_mutex_lock(&j->mu);
+            int len = j->counts[w];
+            int64_t ids64[64];
+            for (int q = 0; q < len; q++) ids64[q] = j->refs[w * j->b + q];
+            topk_insert(j->keys + w * j->b, ids64, &len, j->b, it.key, i);
+            for (int q = 0; q < len; q++) j->refs[w * j->b + q] = (int32_t)ids64[q];
+            j->counts[w] = len;
+            pthread_mutex_unlock(&j->mu);
+        }
+        ms_free(&ms);
+    }
+    tables_free(&tb);
+    return NULL;
+}
+
+void oracle_bridge_lists(const void *X, int64_t N, int d, int dtype, int P, int n, const void *centers, int t,
+                         int b, const uint64_t *sel, int64_t nsel, int32_t *counts, int32_t *refs, double *keys,
+                         int nthreads) {
+    bl_job_t job = {X, centers, N, d, dtype, P, n, t, b, sel, nsel, counts, refs, keys, 0,
+                    PTHREAD_MUTEX_INITIALIZER};
+    for (int64_t i = 0; i < nsel; i++) counts[i] = 0;
+    if (nthreads <= 1) {
+        bl_worker(&job);
+    } else {
+        pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+        for (int q = 0; q < nthreads; q++) pthread_create(&th[q], NULL, bl_worker, &job);
+        for (int q = 0; q < nthreads; q++) pthread_join(th[q], NULL);
+        free(th);
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: ANN search over the augmented neighborhood graph (Sec. 4.2)  */
 /* ------------------------------------------------------------------------ */

@@ -62,6 +62,7 @@ _sig("ann_index_save", [P_, ctypes.c_char_p])
 _sig("ann_index_free", [P_])
 _sig("ann_index_get_info", [P_, ctypes.POINTER(ann_index_info)])
 _sig("ann_index_get_bridges", [P_, P_, P_])
+_sig("ann_index_lookup_bridges", [P_, P_, i64, P_])
 _sig("ann_search_batch", [P_, P_, i64, P_, P_, i32, i32, i32, i32, P_, P_, P_, P_, P_])
 _sig("ann_server_create", [P_, sz, i32, ctypes.POINTER(P_)])
 _sig("ann_server_destroy", [P_])
@@ -71,7 +72,7 @@ _sig("ann_serve_latency", [P_, u64], f64)
 _sig("ann_serve_replay", [P_, P_, P_, P_, i32, P_, P_, P_, P_, P_])
 
 EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_train_centers", "ann_index_create",
-            "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges",
+            "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges", "ann_index_lookup_bridges",
             "ann_search_batch", "ann_server_create", "ann_server_destroy", "ann_serve_submit", "ann_serve_poll",
             "ann_serve_latency", "ann_serve_replay")
 
@@ -204,6 +205,13 @@ class Index:
         refs = np.empty(max(M * b, 1), np.int32)
         check(lib.ann_index_get_bridges(self.handle, ptr(ids), ptr(refs)))
         return ids[:M], refs[:M * b].reshape(M, b)
+
+    def lookup_bridges(self, ids):
+        """Reference lists (-1 padded) of the selected bridge ids."""
+        ids = np.ascontiguousarray(ids, dtype=np.uint64)
+        refs = np.empty((max(len(ids), 1), self.info()["b"]), np.int32)
+        check(lib.ann_index_lookup_bridges(self.handle, ptr(ids), len(ids), ptr(refs)))
+        return refs[:len(ids)]
 
     def free(self):
         if self.handle:

@@ -733,6 +733,32 @@ extern "C" int ann_index_get_bridges(const ann_index *index, uint64_t *ids, int3
     return ANN_OK;
 }
 
+extern "C" int ann_index_lookup_bridges(const ann_index *index, const uint64_t *ids, int64_t nids, int32_t *refs) {
+    ANN_ARG(index && (nids == 0 || (ids && refs)), "index, ids and refs are required");
+    ANN_ARG(nids >= 0, "nids must be >= 0");
+    const DevIndex &dv = index->dev;
+    const uint64_t suf = (uint64_t)ipow(dv.n, dv.P - dv.PA);
+    const uint64_t nb = (uint64_t)ipow(dv.n, dv.P);
+    std::vector<uint32_t> offA(dv.nA + 1);
+    ANN_CUDA(cudaMemcpy(offA.data(), dv.offA, 4 * (dv.nA + 1), cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> leaves;
+    for (int64_t q = 0; q < nids; q++) {
+        int32_t *out = refs + q * dv.b;
+        for (int i = 0; i < dv.b; i++) out[i] = -1;
+        ANN_ARG(ids[q] < nb, "bridge id out of range");
+        const uint64_t a = ids[q] / suf, lf = ids[q] % suf;
+        const uint32_t j0 = offA[a], j1 = offA[a + 1];
+        if (j1 == j0) continue;
+        leaves.resize(j1 - j0);
+        ANN_CUDA(cudaMemcpy(leaves.data(), dv.leaf + j0, 4 * (size_t)(j1 - j0), cudaMemcpyDeviceToHost));
+        const auto it = std::lower_bound(leaves.begin(), leaves.end(), (uint32_t)lf);
+        if (it == leaves.end() || *it != (uint32_t)lf) continue;
+        const int64_t j = j0 + (it - leaves.begin());
+        ANN_CUDA(cudaMemcpy(out, dv.brefs + j * dv.b, 4 * (size_t)dv.b, cudaMemcpyDeviceToHost));
+    }
+    return ANN_OK;
+}
+
 // ---- file format: header, X, graph, centers, bridge ids (uint64), refs (M*b) ----
 struct FileHeader {
     char magic[8];

@@ -142,3 +142,73 @@ def test_gist1m_sampled_uneven_search(gist1m):
     got = keys[sel].view(np.float32).astype(np.float64)
     np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)
     assert np.all(np.isinf(got[~fin]))
+
+
+# ---------------------------------------------------------------------------
+# The largest indexes: SIFT-shaped 10M uint8 (R = 16) and HOG-shaped 4M
+# float32 (R = 16, 330M non-empty bridges).  Their full bridge graphs are too
+# large for the oracle's global sort, so the oracle computes the lists of
+# selected bridge ids (every reference's top-t scan, no sort) and the index
+# is read back for the same ids.
+# ---------------------------------------------------------------------------
+
+def _big_index(workload, R, seed):
+    from paper_1312_3062_gb300 import _build
+    _build.build()
+    from paper_1312_3062_gb300 import ann
+    spec = datagen.WORKLOADS[workload]
+    X = datagen.references(workload)
+    rng = np.random.default_rng(seed)
+    train = np.sort(rng.choice(len(X), 20000, replace=False))
+    dt = np.uint8 if X.dtype == np.uint8 else np.float32
+    C = oracle.round_centers(oracle.kmeans(X[train], spec["P"], spec["n"], 5,
+                                           datagen.kmeans_init_rows(workload, 20000, spec["n"])), dt)
+    Xd = torch.from_numpy(X).cuda()
+    G, _ = ann.ann_build_knn_graph(Xd, R)
+    ix = ann.Index.create(Xd, G, torch.from_numpy(C).cuda(), t=100, b=5)
+    torch.cuda.synchronize()
+    return ann, X, C, G, ix
+
+
+def _selected_bridges(X, C, rng, n_random=400, n_refs=40):
+    """Random bridge ids plus the first bridges of random references (these
+    are chosen by a reference, hence non-empty)."""
+    P, n, dp = C.shape
+    ids = set(int(v) for v in rng.integers(0, n ** P, n_random, dtype=np.uint64))
+    for r in rng.choice(len(X), n_refs, replace=False):
+        x = X[r].astype(np.float64).reshape(P, dp)
+        part = ((C.astype(np.float64) - x[:, None, :]) ** 2).sum(-1)
+        _, bid, _, _ = oracle.multiseq(part, X.dtype, 3)
+        ids.update(int(v) for v in bid)
+    return np.array(sorted(ids), np.uint64)
+
+
+def _check_big(ann, X, C, G, ix, R, seed):
+    rng = np.random.default_rng(seed)
+    rows = rng.choice(len(X), 16, replace=False)
+    ids, _ = oracle.exact_knn(X, X[rows], R + 1)
+    Gs = G[torch.from_numpy(rows).cuda()].cpu().numpy()
+    for i, r in enumerate(rows):
+        np.testing.assert_array_equal(Gs[i], ids[i][ids[i] != r][:R])
+    sel = _selected_bridges(X, C, rng)
+    counts, refs, _ = oracle.bridge_lists(X, C, 100, 5, sel)
+    got = ix.lookup_bridges(sel)
+    np.testing.assert_array_equal(got, refs)
+    assert counts.max() > 0 and counts.min() == 0   # both present and absent ids were checked
+
+
+def test_sift10m_sampled_knn_rows_and_bridge_lists():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ann, X, C, G, ix = _big_index(5, 16, 5055)
+    _check_big(ann, X, C, G, ix, 16, 55)
+    ix.free()
+
+
+def test_hog4m_sampled_knn_rows_and_bridge_lists():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    ann, X, C, G, ix = _big_index(4, 16, 4044)
+    assert ix.info()["groups"] > 0   # dense bridge graph: the c2 group level is built
+    _check_big(ann, X, C, G, ix, 16, 44)
+    ix.free()

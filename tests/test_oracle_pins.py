@@ -489,3 +489,28 @@ def test_on_demand_rows_equal_stored_graph(oracle_lib):
     b = oracle.search(X, 7, C, bg, Qs, 5, 120, trace=True)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[2]["trace"], b[2]["trace"])
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_bridge_lists_of_selected_bridges_equal_the_bridge_graph(oracle_lib, dtype):
+    # the restricted form (no global sort of all N*t triples) agrees with the
+    # full bridge graph on present ids and gives empty lists for absent ids
+    rng = np.random.default_rng(31)
+    X = gmm(rng, 500, 16, 6, 20.0 if dtype == np.uint8 else 0.2, dtype)
+    init = rng.permutation(len(X))[:8]
+    C = oracle.round_centers(oracle.kmeans(X, 4, 8, 4, init), dtype)
+    bg = oracle.bridge_graph(X, C, 30, 3)
+    present = bg["bridges"][rng.choice(len(bg["bridges"]), 40, replace=False)]
+    absent = np.setdiff1d(np.arange(8 ** 4, dtype=np.uint64), bg["bridges"])[:20]
+    sel = np.sort(np.concatenate([present, absent]))
+    counts, refs, keys = oracle.bridge_lists(X, C, 30, 3, sel, nthreads=4)
+    where = {int(v): i for i, v in enumerate(bg["bridges"])}
+    for i, y in enumerate(sel):
+        if int(y) not in where:
+            assert counts[i] == 0 and np.all(refs[i] == -1)
+            continue
+        j = where[int(y)]
+        lo, hi = bg["offsets"][j], bg["offsets"][j + 1]
+        assert counts[i] == hi - lo
+        np.testing.assert_array_equal(refs[i, :counts[i]], bg["refs"][lo:hi])
+        np.testing.assert_array_equal(keys[i, :counts[i]], bg["keys"][lo:hi])
