@@ -36,6 +36,7 @@ constexpr int kCap = 512;  // candidates per row kept for exact rescoring
 
 static std::mutex g_blas_mu;
 static cublasHandle_t g_blas[64];
+static std::mutex g_blas_use[64];  // a handle's stream is set per call: one caller at a time
 
 static int blas_handle(cublasHandle_t *out) {
     int dev = 0;
@@ -274,6 +275,9 @@ int knn_f32_tensor(const float *refs, int64_t N, const float *queries, int64_t n
     cublasHandle_t h;
     int rc = blas_handle(&h);
     if (rc != ANN_OK) return rc;
+    int dev = 0;
+    ANN_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> use(g_blas_use[dev]);
     // tile of query rows: the tile's dot products take at most 2^31 floats
     int64_t tm = std::max<int64_t>(32, std::min<int64_t>(nq, ((int64_t)1 << 31) / N) / 32 * 32);
     if (tm > nq) tm = nq;

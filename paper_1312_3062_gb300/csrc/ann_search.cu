@@ -215,7 +215,11 @@ struct Plan {
     cudaGraphExec_t exec = nullptr;
     int32_t *scratch = nullptr;   // counts[kBuckets] + tickets[kBuckets] + lists[kBuckets*nq]
     uint8_t *wscratch = nullptr;  // per-warp sorted bridge windows (largest windowed bucket's need)
+    uint64_t last_use = 0;        // for evicting the least recently used plan
 };
+
+// plans kept per index; the least recently used one goes beyond this
+static const size_t kMaxPlans = 32;
 
 struct PlanKey {
     const void *queries;
@@ -236,6 +240,7 @@ struct PlanKey {
 
 struct PlanCache {
     std::mutex mu;
+    uint64_t clock = 0;
     std::map<PlanKey, Plan> plans;
     std::map<std::pair<int, int>, Tune> tuned;  // (bucket capacity, kmax) -> measured best launch shape
 };
@@ -505,6 +510,17 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
     PlanKey key{queries, nq, k, T, k_all, T_all, kmax, out_ids, out_keys, out_status, out_stats, s};
     std::lock_guard<std::mutex> g(pc->mu);
     auto it = pc->plans.find(key);
+    if (it == pc->plans.end() && pc->plans.size() >= kMaxPlans) {
+        // evict the least recently used plan once its stream has finished with it
+        auto old = pc->plans.begin();
+        for (auto jt = pc->plans.begin(); jt != pc->plans.end(); ++jt)
+            if (jt->second.last_use < old->second.last_use) old = jt;
+        ANN_CUDA(cudaStreamSynchronize(old->first.stream));
+        cudaGraphExecDestroy(old->second.exec);
+        cudaFree(old->second.scratch);
+        if (old->second.wscratch) cudaFree(old->second.wscratch);
+        pc->plans.erase(old);
+    }
     if (it == pc->plans.end()) {
         Plan p;
         ANN_CUDA(cudaMalloc(&p.scratch, sizeof(int32_t) * (2 * kBuckets + (size_t)kBuckets * nq + 1)));
@@ -562,6 +578,7 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
         }
         it = pc->plans.emplace(key, p).first;
     }
+    it->second.last_use = ++pc->clock;
     ANN_CUDA(cudaGraphLaunch(it->second.exec, s));
     return ANN_OK;
 }

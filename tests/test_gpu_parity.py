@@ -329,3 +329,18 @@ def test_f32_tensor_knn_rows_with_many_ties_fall_back_exactly(ann):
     want_ids, want_keys = oracle.exact_knn(X, Q, 20)
     np.testing.assert_array_equal(ids.cpu().numpy(), want_ids)
     np.testing.assert_allclose(keys.cpu().numpy().astype(np.float64), want_keys, rtol=F32_RTOL, atol=0)
+
+
+def test_persistent_plans_beyond_the_cache_limit_stay_correct(ann, tiny_sift):
+    # every call with fresh output buffers is a new plan; past the cache limit
+    # the least recently used plans are evicted and results do not change
+    X, Q, G, C, bg = tiny_sift
+    ix = ann.Index.create(dev(X), dev(G), dev(C), t=100, b=5, bridges=bg)
+    Qd = dev(Q)
+    want, _, _ = ann.ann_search_batch(ix, Qd, 10, 256, kmax=10, mode=0)
+    want = want.cpu().numpy()
+    for _ in range(40):
+        ids, _, st = ann.ann_search_batch(ix, Qd, 10, 256, kmax=10, mode=1)
+        np.testing.assert_array_equal(ids.cpu().numpy(), want)
+        assert np.all(st.cpu().numpy() == 0)
+    ix.free()
