@@ -184,11 +184,18 @@ enum {
  * -1; out_keys (optional) nq*kmax keys padded with UINT32_MAX / +inf;
  * out_status (optional) int32[nq] with ANN_OK or ANN_ERR_CAPACITY;
  * out_stats (optional) int64[nq*ANN_NSTATS].
- * mode ANN_MODE_PLAIN: kernels launched for this batch on `stream`.
- * mode ANN_MODE_PERSISTENT: queries are bucketed by budget and run by one
- * persistent kernel per bucket pulling work from a device queue, the whole
- * batch replayed as a CUDA graph captured once per (index, shape).
- * Results are identical in both modes.  Asynchronous. */
+ * mode ANN_MODE_PLAIN: one kernel launch for this batch on `stream`, sized
+ * for the largest budget (per-query T costs one device max and a host sync).
+ * mode ANN_MODE_PERSISTENT: queries are bucketed by budget (128 * 2^i) and
+ * each bucket is run by a kernel sized for it, pulling queries from a device
+ * ticket or taking fixed shares; the sequence is captured once per (index,
+ * pointers, sizes, stream) into a CUDA graph and replayed (at most 32 plans
+ * per index, least recently used evicted after its stream finished).  The
+ * first call that meets a (budget bucket, kmax) measures candidate launch
+ * shapes on the batch itself and keeps the fastest for the index; that call
+ * synchronizes `stream` and runs the batch a few times.
+ * Results are identical in both modes and for every launch shape.
+ * Asynchronous except as stated. */
 int ann_search_batch(const ann_index *index, const void *queries, int64_t nq, const int32_t *k,
                      const int32_t *T, int32_t k_all, int32_t T_all, int32_t kmax, int32_t mode,
                      int32_t *out_ids, void *out_keys, int32_t *out_status, int64_t *out_stats,
