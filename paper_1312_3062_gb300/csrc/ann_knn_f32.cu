@@ -190,6 +190,10 @@ __global__ void __launch_bounds__(32 * kSegWarps) f32_cand_kernel(const float *D
     const float qn = qn32[q];
     const double e = eps_row(d, qn64[q], __longlong_as_double((long long)*xmax));
     const double lim = (double)akth[r] + 2.0 * e;
+    // compare in float32 against the limit rounded up: never fewer candidates
+    // than the fp64 comparison (fp64 throughput is low on this part)
+    float limf = (float)lim;
+    if ((double)limf < lim) limf = nextafterf(limf, __int_as_float(0x7f800000));
     const float *row = D + r * N;
     uint32_t *out = cand + r * kCap;
     const int64_t seg = ((N + kSegWarps - 1) / kSegWarps + 31) / 32 * 32;
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(32 * kSegWarps) f32_cand_kernel(const float *D
 #pragma unroll
         for (int u = 0; u < kUnroll; u++) {
             const int64_t c = c0 + 32 * u + lane;
-            const bool take = c < cend && !(exclude_self && c == q) && (double)approx_key(dv[u], qn, xv[u]) <= lim;
+            const bool take = c < cend && !(exclude_self && c == q) && approx_key(dv[u], qn, xv[u]) <= limf;
             const unsigned m = __ballot_sync(0xffffffffu, take);
             if (m) {
                 int base = 0;
