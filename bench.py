@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--build-only", action="store_true", help="build the index and exit (profiling the build)")
     ap.add_argument("--Tlist", default=None, help="workload 4: comma-separated budgets instead of 256,1024,4096")
+    ap.add_argument("--ablation", action="store_true",
+                    help="sift1m: recall@10 and queries/s versus T for the method, for graph search without "
+                         "bridges (one seed), and for other part dictionaries (P x n)")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2 sift1m (default, the headline); 3 gist1m uneven k/T; 4 hog4m recall-vs-T; "
                          "5 sift10m served")
@@ -391,6 +394,8 @@ def main():
         return
     if WORKLOAD != 2:
         return run_other(args, rank, ws, log, torch, ann, datagen, W)
+    if args.ablation:
+        return run_ablation(args, rank, ws, log, torch, ann, datagen, W)
     T90, rec, table = sweep_t90(args, torch, ann, W, log)
     log(f"T90={T90} recall@10={rec:.4f}")
     nq = W["nq"]
@@ -617,6 +622,49 @@ def run_other(args, rank, ws, log, torch, ann, datagen, W):
                 "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
                                                        "bytes_bridges")}, "build_s": W["build_s"]}}
         print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+def run_ablation(args, rank, ws, log, torch, ann, datagen, W):
+    """The paper's ablations on the SIFT-shaped 1M workload, same data, same
+    exact kNN graph, same queries: recall@10 and persistent queries/s versus
+    T for (a) the method (P = 4 x n = 256), (b) best-first graph search
+    without bridges, seeded at one fixed reference (a bridge graph of one
+    bridge holding reference 0), (c) P = 2 x n = 256 and (d) P = 4 x n = 50
+    dictionaries (k-means, 10 iterations, the same initial-row recipe)."""
+    grid = [64, 128, 256, 512, 1024, 2048]
+    X, Q, G = W["X"], W["Q"], W["G"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def curve(ix, name):
+        pts = []
+        for T in grid:
+            ids, _, st = ann.ann_search_batch(ix, Q, K, T, kmax=K, mode=1, stream=stream)
+            torch.cuda.synchronize()
+            rec = recall_at_10(torch, ids, W)
+            t = time_steps(torch, lambda: ann.ann_search_batch(ix, Q, K, T, kmax=K, mode=1, stream=stream),
+                           2, 1, flush, stream)
+            pts.append({"T": T, "recall": rec, "qps": W["nq"] * len(t) / (sum(t) / 1e3)})
+            log(f"{name}: T={T} recall@10={rec:.4f} {pts[-1]['qps']:.0f} q/s")
+        return pts
+
+    out = {"method P=4 x n=256": curve(W["index"], "method 4x256")}
+    seed = {"bridges": np.array([0], np.uint64), "offsets": np.array([0, 1], np.int64),
+            "refs": np.array([0], np.int32)}
+    ix_seed = ann.Index.create(X, G, W["C"], t=100, b=5, bridges=seed)
+    out["graph search, one seed (no bridges)"] = curve(ix_seed, "one seed")
+    ix_seed.free()
+    for P, n in ((2, 256), (4, 50)):
+        C = ann.ann_train_centers(X, P, n, 10, datagen.kmeans_init_rows(WORKLOAD, len(X), n))
+        ix = ann.Index.create(X, G, C, t=100, b=5)
+        inf = ix.info()
+        out[f"method P={P} x n={n} (M={inf['M']}, alpha={inf['alpha']:.3g})"] = curve(ix, f"{P}x{n}")
+        ix.free()
+    if rank == 0:
+        print(json.dumps({"metric": "recall@10 and queries/s versus T (ablation)", "unit": "queries/s",
+                          "workload": f"sift1m: N={W['N']} x 128 uint8, {W['nq']} queries, kNN graph R=20, k=10",
+                          "mode": "persistent", "curves": out}), flush=True)
     barrier(ws)
 
 
