@@ -14,6 +14,10 @@ Functions and the passages they follow:
   bridge_graph   Sec. 4.1 (top-t bridges per ref, top-b refs per bridge)
   search         Sec. 4.2, Algorithm 1 (ANN search over the augmented graph)
   recall_at_k    Sec. 5.1 (accuracy r/k)
+  rp_partition   Sec. 5.3 / 5.5 reading: one random partition of the approximate
+                 neighbourhood-graph construction (recursive median splits)
+  knn_graph_approx  the same reading: leaf brute force over random partitions,
+                 then neighbourhood propagation (rows on demand)
 Every function is pinned by the ``-m "not gpu"`` tests in ``tests/``.
 """
 from __future__ import annotations
@@ -69,6 +73,10 @@ def _load():
                                           i64, P, P, i32, P, P, P, P, i32, i32]
             lib.oracle_search.restype = i32
             lib.oracle_num_stats.restype = i32
+            lib.oracle_rp_partition.argtypes = [P, i64, i32, P, i32, P]
+            lib.oracle_rp_partition.restype = None
+            lib.oracle_knn_graph_approx.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P]
+            lib.oracle_knn_graph_approx.restype = None
             _lib = lib
     return _lib
 
@@ -260,3 +268,46 @@ def recall_at_k(found_ids: np.ndarray, true_keys: np.ndarray, X: np.ndarray, que
             dk = (diff * diff).sum(1).astype(np.float32).astype(np.float64)
         out[i] = np.count_nonzero(dk <= kth) / k
     return out
+
+
+def _levels_of(dirs: np.ndarray) -> int:
+    nseg = dirs.shape[1]
+    levels = (nseg + 1).bit_length() - 1
+    assert (1 << levels) - 1 == nseg, "dirs must hold 2^levels - 1 directions per round"
+    return levels
+
+
+def rp_partition(X: np.ndarray, dirs_round: np.ndarray) -> np.ndarray:
+    """One random partition of the approximate graph construction: the point
+    at every position after the recursive median splits along dirs_round
+    (shape (2^levels - 1, d), int8).  Leaves are the 2^levels segments of
+    the recursive halving of [0, N)."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    assert X.dtype == np.uint8
+    dirs_round = np.ascontiguousarray(dirs_round, dtype=np.int8)
+    levels = _levels_of(dirs_round[None])
+    perm = np.empty(X.shape[0], np.int32)
+    lib.oracle_rp_partition(_ptr(X), X.shape[0], X.shape[1], _ptr(dirs_round), levels, _ptr(perm))
+    return perm
+
+
+def knn_graph_approx(X: np.ndarray, R: int, dirs: np.ndarray, iters: int, rows=None):
+    """Approximate R-NN graph of uint8 rows: leaf brute force over
+    dirs.shape[0] random partitions, then `iters` propagation steps.
+    dirs: (rounds, 2^levels - 1, d) int8.  rows: the points whose rows are
+    wanted (None = all).  Returns (ids int32, keys float64), each (nrows, R),
+    ascending (key, id)."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    assert X.dtype == np.uint8 and R <= 64
+    dirs = np.ascontiguousarray(dirs, dtype=np.int8)
+    rounds, levels = dirs.shape[0], _levels_of(dirs)
+    assert dirs.shape[2] == X.shape[1]
+    sel = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    nrows = X.shape[0] if sel is None else len(sel)
+    ids = np.empty((nrows, R), np.int32)
+    keys = np.empty((nrows, R), np.float64)
+    lib.oracle_knn_graph_approx(_ptr(X), X.shape[0], X.shape[1], R, _ptr(dirs), rounds, levels, iters,
+                                None if sel is None else _ptr(sel), nrows, _ptr(ids), _ptr(keys))
+    return ids, keys

@@ -921,3 +921,204 @@ int oracle_search(const void *X, int64_t N, int d, int dtype, const int32_t *gra
 }
 
 int oracle_num_stats(void) { return ST_N; }
+
+/* ------------------------------------------------------------------------ */
+/* Approximate R-NN neighbourhood graph.  Sec. 5.3 builds the neighbourhood */
+/* graph approximately with the construction of its reference [WangWZTGL12] */
+/* (random divide-and-conquer, then neighbourhood propagation) and Sec. 5.5 */
+/* puts its cost at O(N log N); the paper gives no steps.  The reading      */
+/* fixed here, for uint8 data:                                              */
+/*  - `rounds` random partitions.  Positions [0, N) are halved recursively  */
+/*    `levels` times: segment [lo, hi) has the children [lo, m) and         */
+/*    [m, hi), m = lo + (hi - lo) / 2 (integer division).  Level l holds     */
+/*    the 2^l segments s = 0 .. 2^l - 1, left to right.  Starting from the  */
+/*    identity order, at each level l every segment s reorders its members  */
+/*    ascending by (<u, x>, id), u = dirs[round][2^l - 1 + s] (d int8       */
+/*    entries, a random direction drawn by the caller).  The 2^levels       */
+/*    segments below the last level are the leaves.                         */
+/*  - Leaf step: every point is offered every other member of its leaf, in  */
+/*    every round.                                                          */
+/*  - `iters` propagation steps, each from the rows of the step before:     */
+/*    row i is offered every entry of the rows of its neighbours (i itself  */
+/*    excluded).                                                            */
+/* Offering (key, id) keeps the R smallest (key, id) pairs with distinct    */
+/* ids, so a row is the R best of every candidate offered, in any order.    */
+/* ------------------------------------------------------------------------ */
+
+/* The range [lo, hi) of segment s at level l of the recursive halving. */
+static void seg_range(int64_t N, int l, int64_t s, int64_t *lo, int64_t *hi) {
+    int64_t a = 0, b = N;
+    for (int bit = l - 1; bit >= 0; bit--) {
+        int64_t m = a + (b - a) / 2;
+        if ((s >> bit) & 1) a = m;
+        else b = m;
+    }
+    *lo = a;
+    *hi = b;
+}
+
+typedef struct {
+    int64_t proj, id;
+} proj_id_t;
+
+static int proj_id_cmp(const void *a, const void *b) {
+    const proj_id_t *x = (const proj_id_t *)a, *y = (const proj_id_t *)b;
+    if (x->proj != y->proj) return x->proj < y->proj ? -1 : 1;
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* One random partition: perm[p] = the point at position p after `levels`
+   levels of median splits along the directions dirs[(2^l - 1 + s) * d]. */
+void oracle_rp_partition(const uint8_t *X, int64_t N, int d, const int8_t *dirs, int levels, int32_t *perm) {
+    for (int64_t i = 0; i < N; i++) perm[i] = (int32_t)i;
+    proj_id_t *buf = (proj_id_t *)malloc(sizeof(proj_id_t) * (size_t)(N > 0 ? N : 1));
+    for (int l = 0; l < levels; l++) {
+        for (int64_t s = 0; s < ((int64_t)1 << l); s++) {
+            int64_t lo, hi;
+            seg_range(N, l, s, &lo, &hi);
+            const int8_t *u = dirs + ((((int64_t)1 << l) - 1) + s) * d;
+            for (int64_t p = lo; p < hi; p++) {
+                const uint8_t *x = X + (int64_t)perm[p] * d;
+                int64_t acc = 0;
+                for (int w = 0; w < d; w++) acc += (int64_t)u[w] * (int64_t)x[w];
+                buf[p - lo].proj = acc;
+                buf[p - lo].id = perm[p];
+            }
+            qsort(buf, (size_t)(hi - lo), sizeof(proj_id_t), proj_id_cmp);
+            for (int64_t p = lo; p < hi; p++) perm[p] = (int32_t)buf[p - lo].id;
+        }
+    }
+    free(buf);
+}
+
+/* offer (key, id) to a row: keep the cap smallest pairs, ids distinct */
+static void offer_distinct(double *keys, int64_t *ids, int *len, int cap, double key, int64_t id) {
+    for (int r = 0; r < *len; r++)
+        if (ids[r] == id) return;
+    topk_insert(keys, ids, len, cap, key, id);
+}
+
+/* Rows of every propagation step, computed on demand and kept. */
+typedef struct {
+    int64_t cap, used;
+    int32_t *slot;  /* N entries: index into the pool, -1 if not computed */
+    int64_t *ids;   /* pool, cap * R */
+    double *keys;
+    int *len;
+} row_store_t;
+
+typedef struct {
+    const uint8_t *X;
+    int64_t N;
+    int d, R, rounds, levels;
+    int32_t *perm; /* rounds * N: point at each position */
+    int32_t *pos;  /* rounds * N: position of each point */
+    row_store_t *st; /* iters + 1 stores */
+} approx_t;
+
+static int64_t store_new(row_store_t *s, int R) {
+    if (s->used == s->cap) {
+        s->cap = s->cap ? 2 * s->cap : 1024;
+        s->ids = (int64_t *)realloc(s->ids, sizeof(int64_t) * (size_t)(s->cap * R));
+        s->keys = (double *)realloc(s->keys, sizeof(double) * (size_t)(s->cap * R));
+        s->len = (int *)realloc(s->len, sizeof(int) * (size_t)s->cap);
+    }
+    return s->used++;
+}
+
+/* Row of point i after step it (0 = leaf step); copies it to keys/ids/len. */
+static void approx_row(approx_t *g, int it, int64_t i, double *keys, int64_t *ids, int *len) {
+    row_store_t *s = &g->st[it];
+    const int R = g->R;
+    if (s->slot[i] < 0) {
+        double k0[64];
+        int64_t i0[64];
+        int n0 = 0;
+        const uint8_t *xi = g->X + i * g->d;
+        if (it == 0) {
+            for (int r = 0; r < g->rounds; r++) {
+                int64_t p = g->pos[(int64_t)r * g->N + i], lo = 0, hi = g->N;
+                for (int l = 0; l < g->levels; l++) {
+                    int64_t m = lo + (hi - lo) / 2;
+                    if (p >= m) lo = m;
+                    else hi = m;
+                }
+                for (int64_t q = lo; q < hi; q++) {
+                    int64_t j = g->perm[(int64_t)r * g->N + q];
+                    if (j == i) continue;
+                    offer_distinct(k0, i0, &n0, R, sqdist(xi, g->X + j * g->d, g->d, DT_U8), j);
+                }
+            }
+        } else {
+            double kb[64];
+            int64_t ib[64];
+            int nb = 0;
+            approx_row(g, it - 1, i, kb, ib, &nb);
+            for (int r = 0; r < nb; r++) offer_distinct(k0, i0, &n0, R, kb[r], ib[r]);
+            for (int r = 0; r < nb; r++) {
+                double kj[64];
+                int64_t ij[64];
+                int nj = 0;
+                approx_row(g, it - 1, ib[r], kj, ij, &nj);
+                for (int c = 0; c < nj; c++) {
+                    if (ij[c] == i) continue;
+                    offer_distinct(k0, i0, &n0, R, sqdist(xi, g->X + ij[c] * g->d, g->d, DT_U8), ij[c]);
+                }
+            }
+        }
+        int64_t at = store_new(s, R);
+        memcpy(s->keys + at * R, k0, sizeof(double) * (size_t)n0);
+        memcpy(s->ids + at * R, i0, sizeof(int64_t) * (size_t)n0);
+        s->len[at] = n0;
+        s->slot[i] = (int32_t)at;
+    }
+    int64_t at = s->slot[i];
+    *len = s->len[at];
+    memcpy(keys, s->keys + at * R, sizeof(double) * (size_t)*len);
+    memcpy(ids, s->ids + at * R, sizeof(int64_t) * (size_t)*len);
+}
+
+/* Approximate R-NN graph rows (the reading above).  dirs: rounds *
+   (2^levels - 1) * d int8.  rows: the points whose rows are wanted (NULL =
+   all N, in order); out: nrows * R ids / keys, ascending (key, id), padded
+   with -1 / +inf.  Rows are evaluated on demand, so a few sampled rows of a
+   large set cost only their own dependencies.  R <= 64. */
+void oracle_knn_graph_approx(const uint8_t *X, int64_t N, int d, int R, const int8_t *dirs, int rounds,
+                             int levels, int iters, const int64_t *rows, int64_t nrows, int32_t *out_ids,
+                             double *out_keys) {
+    approx_t g = {X, N, d, R, rounds, levels, NULL, NULL, NULL};
+    g.perm = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rounds * N));
+    g.pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)(rounds * N));
+    const int64_t nseg = ((int64_t)1 << levels) - 1;
+    for (int r = 0; r < rounds; r++) {
+        int32_t *pm = g.perm + (int64_t)r * N;
+        oracle_rp_partition(X, N, d, dirs + (int64_t)r * nseg * d, levels, pm);
+        for (int64_t p = 0; p < N; p++) g.pos[(int64_t)r * N + pm[p]] = (int32_t)p;
+    }
+    g.st = (row_store_t *)calloc((size_t)iters + 1, sizeof(row_store_t));
+    for (int it = 0; it <= iters; it++) {
+        g.st[it].slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+        for (int64_t i = 0; i < N; i++) g.st[it].slot[i] = -1;
+    }
+    if (!rows) nrows = N;
+    for (int64_t q = 0; q < nrows; q++) {
+        int64_t i = rows ? rows[q] : q;
+        double k[64];
+        int64_t id[64];
+        int n = 0;
+        approx_row(&g, iters, i, k, id, &n);
+        for (int r = 0; r < R; r++) {
+            out_ids[q * R + r] = r < n ? (int32_t)id[r] : -1;
+            out_keys[q * R + r] = r < n ? k[r] : INFINITY;
+        }
+    }
+    for (int it = 0; it <= iters; it++) {
+        free(g.st[it].slot);
+        free(g.st[it].ids);
+        free(g.st[it].keys);
+        free(g.st[it].len);
+    }
+    free(g.st);
+    free(g.perm);
+    free(g.pos);
+}

@@ -146,6 +146,23 @@ def mixture(seed: int, N: int, d: int, ncomp: int, dtype) -> np.ndarray:
     return (x / np.linalg.norm(x, axis=1, keepdims=True)).astype(np.float32)
 
 
+def rp_directions(seed: int, rounds: int, levels: int, d: int) -> np.ndarray:
+    """Random split directions for the approximate kNN-graph construction:
+    int8 entries +-1 (Rademacher), shape (rounds, 2^levels - 1, d), one per
+    segment of every level of every round."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([SEED_BASE, 50, seed])))
+    signs = rng.integers(0, 2, size=(rounds, (1 << levels) - 1, d), dtype=np.int8)
+    return (2 * signs - 1).astype(np.int8)
+
+
+def rp_levels(N: int, leaf_max: int) -> int:
+    """Smallest number of halvings after which no leaf exceeds leaf_max points."""
+    levels = 0
+    while -(-N // (1 << levels)) > leaf_max:
+        levels += 1
+    return levels
+
+
 def poisson_requests(workload: int, nreq: int, rate_qps: float, seed_salt: int = 30):
     """Poisson arrivals of request batches: (arrival_s, batch_size) arrays;
     batch sizes log-uniform integers in [1, 512]."""
