@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--ablation", action="store_true",
                     help="sift1m: recall@10 and queries/s versus T for the method, for graph search without "
                          "bridges (one seed), and for other part dictionaries (P x n)")
+    ap.add_argument("--knn-approx", action="store_true",
+                    help="workload 2 or 5: approximate kNN graph versus the exact one (build time, graph "
+                         "recall; on workload 2 also the search each graph gives)")
     ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
                     help="2 sift1m (default, the headline); 3 gist1m uneven k/T; 4 hog4m recall-vs-T; "
                          "5 sift10m served")
@@ -388,6 +391,8 @@ def main():
     barrier(ws)
     from paper_1312_3062_gb300 import ann, datagen
 
+    if args.knn_approx:
+        return run_knn_approx(args, rank, ws, log, torch, ann, datagen)
     W = build_workload(args, torch, ann, datagen, log)
     if args.build_only:
         torch.cuda.synchronize()
@@ -666,6 +671,85 @@ def run_ablation(args, rank, ws, log, torch, ann, datagen, W):
                           "workload": f"sift1m: N={W['N']} x 128 uint8, {W['nq']} queries, kNN graph R=20, k=10",
                           "mode": "persistent", "curves": out}), flush=True)
     barrier(ws)
+
+
+def run_knn_approx(args, rank, ws, log, torch, ann, datagen):
+    """The approximate neighbourhood graph (the construction Sec. 5.3 uses,
+    read as random median-split partitions, leaf brute force and
+    neighbourhood propagation) against the exact graph of the same data:
+    build time (CUDA events on the launching stream, L2 flushed between
+    builds), graph recall (share of the exact R neighbours found: all rows on
+    workload 2, 10,000 sampled rows on workload 5) and, on workload 2, the
+    search each graph gives (recall@10, persistent queries/s at T = 512)."""
+    if rank != 0:
+        return
+    if WORKLOAD not in (2, 5):
+        raise SystemExit("--knn-approx runs on workload 2 or 5")
+    spec = datagen.WORKLOADS[WORKLOAD]
+    R = spec["R"]
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    steps = max(1, min(args.steps, 3))
+    out = {"metric": "approximate kNN graph: build seconds and graph recall", "unit": "s",
+           "workload": None, "settings": []}
+    if WORKLOAD == 2:
+        W = build_workload(args, torch, ann, datagen, log)
+        X, E = W["X"], W["G"]
+        N, d = X.shape
+        ex_ids = torch.empty((N, R), dtype=torch.int32, device="cuda")
+        t = time_steps(torch, lambda: ann.ann_build_knn_graph(X, R, out_ids=ex_ids, stream=stream), steps, 1,
+                       flush, stream)
+        out["exact_build_s"] = float(np.median(t)) / 1e3
+        rows = None
+    else:
+        N = args.N or spec["N"]
+        t0 = time.time()
+        X = torch.from_numpy(datagen.references(WORKLOAD, N)).cuda()
+        N, d = X.shape
+        log(f"data {N}x{d} in {time.time() - t0:.1f}s")
+        rows = torch.from_numpy(np.sort(np.random.default_rng(9).choice(N, 10000, replace=False))).cuda()
+        cand, _ = ann.ann_exact_knn(X, X[rows].contiguous(), R + 1)
+        keep = cand.long() != rows[:, None]
+        E = torch.stack([c[m][:R] for c, m in zip(cand.long(), keep)])
+        out["exact_build_s"] = None
+    out["workload"] = f"{spec['name']}: N={N} x {d} uint8, R={R}"
+
+    def graph_recall(A):
+        A = A.long() if rows is None else A[rows].long()
+        hit = 0
+        for c0 in range(0, A.shape[0], 1 << 18):
+            a, e = A[c0:c0 + (1 << 18)], E[c0:c0 + (1 << 18)].long()
+            hit += int((a[:, :, None] == e[:, None, :]).any(-1).sum().item())
+        return hit / (A.shape[0] * R)
+
+    def search_point(ix):
+        ids, _, _ = ann.ann_search_batch(ix, W["Q"], K, 512, kmax=K, mode=1, stream=stream)
+        torch.cuda.synchronize()
+        rec = recall_at_10(torch, ids, W)
+        t = time_steps(torch, lambda: ann.ann_search_batch(ix, W["Q"], K, 512, kmax=K, mode=1, stream=stream),
+                       2, 1, flush, stream)
+        return {"recall_at_10": rec, "qps": W["nq"] * len(t) / (sum(t) / 1e3)}
+
+    if WORKLOAD == 2:
+        out["exact_search_T512"] = search_point(W["index"])
+        log(f"exact graph {out['exact_build_s']:.3f}s; search T=512 {out['exact_search_T512']}")
+    ids = torch.empty((N, R), dtype=torch.int32, device="cuda")
+    keys = torch.empty((N, R), dtype=torch.int32, device="cuda")
+    for rounds, leaf_max, iters in ((4, 1024, 1), (8, 1024, 1), (4, 1024, 2), (8, 1024, 2)):
+        levels = datagen.rp_levels(N, leaf_max)
+        dirs = torch.from_numpy(datagen.rp_directions(0, rounds, levels, d)).cuda()
+        t = time_steps(torch, lambda: ann.ann_build_knn_graph_approx(X, R, dirs, iters, out_ids=ids,
+                                                                     out_keys=keys, stream=stream),
+                       steps, 1, flush, stream)
+        e = {"rounds": rounds, "levels": levels, "largest_leaf": -(-N // (1 << levels)), "iters": iters,
+             "build_s": float(np.median(t)) / 1e3, "graph_recall": graph_recall(ids)}
+        if WORKLOAD == 2:
+            ix = ann.Index.create(X, ids, W["C"], t=spec["t"], b=spec["b"])
+            e["search_T512"] = search_point(ix)
+            ix.free()
+        log(f"approx {e}")
+        out["settings"].append(e)
+    print(json.dumps(out), flush=True)
 
 
 def reference_arm(args, rank, ws, log):

@@ -94,6 +94,34 @@ int ann_exact_knn_static(const void *refs, int64_t N, const void *queries, int64
 int ann_build_knn_graph(const void *data, int dtype, int64_t N, int32_t d, int32_t R,
                         int32_t *out_ids, void *out_keys, void *stream);
 
+/* Approximate R-NN neighbourhood graph of uint8 data.  Sec. 5.3 builds its
+ * graphs with an approximate construction (random divide-and-conquer, then
+ * neighbourhood propagation; cost O(N log N), Sec. 5.5) and gives no steps;
+ * this call fixes them:
+ *  1. For each of `rounds` random partitions: positions [0, N) are halved
+ *     recursively `levels` times (segment [lo, hi) has the children [lo, m)
+ *     and [m, hi), m = lo + (hi - lo) / 2); starting from the identity
+ *     order, at level l every segment s = 0 .. 2^l - 1 (left to right)
+ *     reorders its members ascending by (<u, x>, id) with
+ *     u = dirs[round][2^l - 1 + s].  The 2^levels final segments are leaves;
+ *     every point is offered every other member of its leaf.
+ *  2. `iters` propagation steps, each reading the rows of the step before:
+ *     row i is offered every entry of its neighbours' rows (i excluded).
+ * A row keeps the R smallest offered (key, id) pairs with distinct ids, so
+ * the result is deterministic.  data: device N*d uint8, 16-byte aligned.
+ * dirs: device int8[rounds][2^levels - 1][d], 16-byte aligned (random split
+ * directions drawn by the caller; NULL allowed when levels == 0).  out_ids:
+ * device int32[N*R]; out_keys: device uint32[N*R] or NULL.  Rows ascending
+ * (key, id).  Requires dtype == ANN_U8, d % 16 == 0, R <= 32, every leaf
+ * >= R + 1 points (floor(N / 2^levels) > R) and the largest leaf,
+ * ceil(N / 2^levels) rows of d + 20 bytes, within one CTA's shared memory
+ * (about 1,500 rows at d = 128); otherwise ANN_ERR_ARG.  Allocates its
+ * scratch (16 N bytes of sort keys, 8 N R bytes per graph copy) with
+ * cudaMallocAsync on `stream`.  Asynchronous. */
+int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N, int32_t d, int32_t R,
+                               const int8_t *dirs, int32_t rounds, int32_t levels, int32_t iters,
+                               int32_t *out_ids, void *out_keys, void *stream);
+
 /* Per-part dictionaries for the bridge vectors (Sec. 4.1, "Computing bridge
  * vectors": product quantization, i.e. k-means on each of the P contiguous
  * parts of d/P dims).  Lloyd's algorithm in fp64: center j of every part

@@ -55,6 +55,7 @@ _sig("ann_last_error", [], ctypes.c_char_p)
 _sig("ann_exact_knn", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_])
 _sig("ann_exact_knn_static", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_])
 _sig("ann_build_knn_graph", [P_, ctypes.c_int, i64, i32, i32, P_, P_, P_])
+_sig("ann_build_knn_graph_approx", [P_, ctypes.c_int, i64, i32, i32, P_, i32, i32, i32, P_, P_, P_])
 _sig("ann_train_centers", [P_, ctypes.c_int, i64, i32, i32, i32, i32, P_, P_, P_, P_])
 _sig("ann_index_create", [ctypes.POINTER(ann_index_desc), ctypes.POINTER(P_)])
 _sig("ann_index_load", [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(P_)])
@@ -71,7 +72,8 @@ _sig("ann_serve_poll", [P_, u64, P_, P_, P_])
 _sig("ann_serve_latency", [P_, u64], f64)
 _sig("ann_serve_replay", [P_, P_, P_, P_, i32, P_, P_, P_, P_, P_])
 
-EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_train_centers", "ann_index_create",
+EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_build_knn_graph_approx",
+            "ann_train_centers", "ann_index_create",
             "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges", "ann_index_lookup_bridges",
             "ann_search_batch", "ann_server_create", "ann_server_destroy", "ann_serve_submit", "ann_serve_poll",
             "ann_serve_latency", "ann_serve_replay")
@@ -145,6 +147,23 @@ def ann_build_knn_graph(data, R, out_ids=None, out_keys=None, stream=None):
                                device=data.device)
     check(lib.ann_build_knn_graph(ptr(data), dtype_code(data), N, d, R, ptr(out_ids), ptr(out_keys),
                                   stream_ptr(stream)))
+    return out_ids, out_keys
+
+
+def ann_build_knn_graph_approx(data, R, dirs, iters, out_ids=None, out_keys=None, stream=None):
+    """dirs: device int8 tensor (rounds, 2^levels - 1, d) of split directions."""
+    import torch
+    N, d = data.shape
+    rounds, nseg = dirs.shape[0], dirs.shape[1]
+    levels = (nseg + 1).bit_length() - 1
+    if (1 << levels) - 1 != nseg or dirs.shape[2] != d:
+        raise ValueError("dirs must have shape (rounds, 2^levels - 1, d)")
+    if out_ids is None:
+        out_ids = torch.empty((N, R), dtype=torch.int32, device=data.device)
+    if out_keys is None:
+        out_keys = torch.empty((N, R), dtype=torch.int32, device=data.device)
+    check(lib.ann_build_knn_graph_approx(ptr(data), dtype_code(data), N, d, R, ptr(dirs) if nseg else None,
+                                         rounds, levels, iters, ptr(out_ids), ptr(out_keys), stream_ptr(stream)))
     return out_ids, out_keys
 
 

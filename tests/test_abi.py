@@ -47,3 +47,14 @@ def test_argument_errors_need_no_gpu(libpath):
     assert b"N or nq" in ann.lib.ann_last_error()
     rc = ann.lib.ann_search_batch(None, None, 1, None, None, 1, 1, 1, 0, None, None, None, None, None)
     assert rc == ann.ANN_ERR_ARG and b"index is NULL" in ann.lib.ann_last_error()
+    # approximate graph: dtype, leaf size, d and alignment are checked on the
+    # host; the (never dereferenced) addresses only have to look aligned
+    cases = [((16, ann.ANN_F32, 1000, 128, 10, 32, 1, 2, 0, 48), b"ANN_U8"),
+             ((16, ann.ANN_U8, 1000, 128, 10, 32, 1, 7, 0, 48), b"R + 1"),
+             ((16, ann.ANN_U8, 1000, 120, 10, 32, 1, 2, 0, 48), b"multiple of 16"),
+             ((8, ann.ANN_U8, 1000, 128, 10, 32, 1, 2, 0, 48), b"16-byte aligned"),
+             ((16, ann.ANN_U8, 1000, 128, 33, 32, 1, 2, 0, 48), b"R must be"),
+             ((16, ann.ANN_U8, 1000, 128, 10, None, 1, 2, 0, 48), b"dirs are required")]
+    for a, msg in cases:
+        rc = ann.lib.ann_build_knn_graph_approx(*a, None, None)
+        assert rc == ann.ANN_ERR_ARG and msg in ann.lib.ann_last_error(), (a, ann.lib.ann_last_error())
