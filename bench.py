@@ -735,7 +735,11 @@ def run_knn_approx(args, rank, ws, log, torch, ann, datagen):
         log(f"exact graph {out['exact_build_s']:.3f}s; search T=512 {out['exact_search_T512']}")
     ids = torch.empty((N, R), dtype=torch.int32, device="cuda")
     keys = torch.empty((N, R), dtype=torch.int32, device="cuda")
-    for rounds, leaf_max, iters in ((4, 1024, 1), (8, 1024, 1), (4, 1024, 2), (8, 1024, 2)):
+    # (rounds, largest leaf allowed, propagation steps); on the 10M set the
+    # mixture's components hold ~10,000 points, so leaves that size matter
+    settings = ((4, 1024, 1), (8, 1024, 1), (4, 1024, 2), (8, 1024, 2)) if WORKLOAD == 2 else \
+        ((4, 1024, 1), (4, 10000, 1), (8, 10000, 1), (8, 10000, 2), (8, 5000, 2))
+    for rounds, leaf_max, iters in settings:
         levels = datagen.rp_levels(N, leaf_max)
         dirs = torch.from_numpy(datagen.rp_directions(0, rounds, levels, d)).cuda()
         t = time_steps(torch, lambda: ann.ann_build_knn_graph_approx(X, R, dirs, iters, out_ids=ids,

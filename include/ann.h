@@ -113,9 +113,10 @@ int ann_build_knn_graph(const void *data, int dtype, int64_t N, int32_t d, int32
  * directions drawn by the caller; NULL allowed when levels == 0).  out_ids:
  * device int32[N*R]; out_keys: device uint32[N*R] or NULL.  Rows ascending
  * (key, id).  Requires dtype == ANN_U8, d % 16 == 0, R <= 32, every leaf
- * >= R + 1 points (floor(N / 2^levels) > R) and the largest leaf,
- * ceil(N / 2^levels) rows of d + 20 bytes, within one CTA's shared memory
- * (about 1,500 rows at d = 128); otherwise ANN_ERR_ARG.  Allocates its
+ * >= R + 1 points (floor(N / 2^levels) > R), and either d <= 128 (leaves of
+ * any size; those beyond shared memory are streamed through it) or the
+ * largest leaf, ceil(N / 2^levels) rows of d + 20 bytes, within one CTA's
+ * shared memory; otherwise ANN_ERR_ARG.  Allocates its
  * scratch (16 N bytes of sort keys, 8 N R bytes per graph copy) with
  * cudaMallocAsync on `stream`.  Asynchronous. */
 int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N, int32_t d, int32_t R,

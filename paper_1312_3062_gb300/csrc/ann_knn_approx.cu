@@ -10,8 +10,10 @@
 //     of the 64-bit keys (segment, <u, x> + bias, id) over all N positions:
 //     a segment's members occupy the same positions before and after, so a
 //     global sort is the per-segment sort.
-//  2. Leaf step: one CTA per leaf stages the leaf's rows in shared memory and
-//     offers every point every other leaf member (one warp per point).
+//  2. Leaf step: every point is offered every other leaf member.  A leaf that
+//     fits in shared memory is staged whole by one CTA (one warp per point);
+//     a larger one (d <= 128) is streamed through shared memory by CTAs of
+//     32 members each, two per warp.
 //  3. `iters` propagation steps (one warp per point): row i is offered the
 //     rows of its neighbours, read from the previous step's graph.
 // A row is a warp-held ascending list of packed (key << 32 | id) values, one
@@ -33,6 +35,9 @@ namespace {
 
 constexpr int LEAF_THREADS = 512;
 constexpr int PROP_THREADS = 256;
+constexpr int TILE_THREADS = 512;
+constexpr int TILE_I = 2 * TILE_THREADS / 32;  // members per CTA of the streamed leaf kernel
+constexpr int TILE_J = 256;                    // leaf rows per shared-memory pass
 constexpr unsigned FULL = 0xffffffffu;
 
 // sum of x_b * u_b over 4 byte pairs: x unsigned, u signed (PTX dp4a with
@@ -162,6 +167,103 @@ __global__ void __launch_bounds__(LEAF_THREADS) rp_leaf_kernel(const uint8_t *__
     }
 }
 
+__device__ __forceinline__ uint32_t dot16(uint4 a, uint4 b, uint32_t acc) {
+    acc = __dp4a(a.x, b.x, acc);
+    acc = __dp4a(a.y, b.y, acc);
+    acc = __dp4a(a.z, b.z, acc);
+    acc = __dp4a(a.w, b.w, acc);
+    return acc;
+}
+
+// leaves larger than shared memory (d <= 128): CTA (leaf, chunk) owns TILE_I
+// members, two per warp with their rows in registers, and streams the whole
+// leaf through shared memory TILE_J rows at a time.  Keys are
+// ||x||^2 + ||y||^2 - 2 x.y in exact integers (the squared distance itself).
+__global__ void __launch_bounds__(TILE_THREADS) rp_leaf_tiled_kernel(const uint8_t *__restrict__ X, int64_t N,
+                                                                     int d, int R, int levels, int chunks,
+                                                                     const uint64_t *__restrict__ sorted,
+                                                                     uint64_t idmask, uint64_t *__restrict__ rows) {
+    extern __shared__ __align__(16) uint8_t sm[];
+    const int64_t leaf = blockIdx.x / chunks;
+    const int chunk = (int)(blockIdx.x % chunks);
+    int64_t lo = 0, hi = N;
+    for (int k = levels - 1; k >= 0; k--) {
+        const int64_t m = lo + (hi - lo) / 2;
+        if ((leaf >> k) & 1) lo = m;
+        else hi = m;
+    }
+    const int S = (int)(hi - lo);
+    const int W = d / 16;
+    const int stride = d + 16;
+    uint32_t *tids = (uint32_t *)(sm + (size_t)TILE_J * stride);
+    uint32_t *tnorm = tids + TILE_J;
+    const int lane = lane_id(), warp = threadIdx.x >> 5;
+    const int i1 = chunk * TILE_I + 2 * warp, i2 = i1 + 1;
+    const bool v1 = i1 < S, v2 = i2 < S;  // warp-uniform
+    const uint32_t g1 = v1 ? (sorted ? (uint32_t)(sorted[lo + i1] & idmask) : (uint32_t)(lo + i1)) : 0u;
+    const uint32_t g2 = v2 ? (sorted ? (uint32_t)(sorted[lo + i2] & idmask) : (uint32_t)(lo + i2)) : 0u;
+    uint4 a1[8], a2[8];
+    uint32_t n1 = 0, n2 = 0;
+#pragma unroll
+    for (int w = 0; w < 8; w++) {
+        a1[w] = make_uint4(0, 0, 0, 0);
+        a2[w] = make_uint4(0, 0, 0, 0);
+        if (w < W) {
+            if (v1) a1[w] = __ldg((const uint4 *)(X + (int64_t)g1 * d) + w);
+            if (v2) a2[w] = __ldg((const uint4 *)(X + (int64_t)g2 * d) + w);
+            n1 = dot16(a1[w], a1[w], n1);
+            n2 = dot16(a2[w], a2[w], n2);
+        }
+    }
+    uint64_t m1 = (v1 && lane < R) ? rows[(int64_t)g1 * R + lane] : ~0ull;
+    uint64_t m2 = (v2 && lane < R) ? rows[(int64_t)g2 * R + lane] : ~0ull;
+    for (int t0 = 0; t0 < S; t0 += TILE_J) {
+        const int TJ = min(TILE_J, S - t0);
+        __syncthreads();  // the previous tile is consumed
+        for (int m = threadIdx.x; m < TJ; m += blockDim.x)
+            tids[m] = sorted ? (uint32_t)(sorted[lo + t0 + m] & idmask) : (uint32_t)(lo + t0 + m);
+        __syncthreads();
+        for (int e = threadIdx.x; e < TJ * W; e += blockDim.x) {
+            const int m = e / W, w = e - m * W;
+            *(uint4 *)(sm + (size_t)m * stride + 16 * w) = __ldg((const uint4 *)(X + (int64_t)tids[m] * d) + w);
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < TJ; m += blockDim.x) {
+            const uint4 *r = (const uint4 *)(sm + (size_t)m * stride);
+            uint32_t n = 0;
+            for (int w = 0; w < W; w++) {
+                const uint4 b = r[w];
+                n = dot16(b, b, n);
+            }
+            tnorm[m] = n;
+        }
+        __syncthreads();
+        if (!v1) continue;  // warp-uniform; the barriers above are reached by every warp
+        for (int jb = 0; jb < TJ; jb += 32) {
+            const int jl = jb + lane, j = t0 + jl;
+            uint64_t c1 = ~0ull, c2 = ~0ull;
+            if (jl < TJ) {
+                const uint4 *rj = (const uint4 *)(sm + (size_t)jl * stride);
+                uint32_t d1 = 0, d2 = 0;
+#pragma unroll
+                for (int w = 0; w < 8; w++)
+                    if (w < W) {
+                        const uint4 b = rj[w];
+                        d1 = dot16(a1[w], b, d1);
+                        d2 = dot16(a2[w], b, d2);
+                    }
+                const uint32_t nj = tnorm[jl], idj = tids[jl];
+                if (j != i1) c1 = ((uint64_t)(n1 + nj - 2u * d1) << 32) | idj;
+                if (v2 && j != i2) c2 = ((uint64_t)(n2 + nj - 2u * d2) << 32) | idj;
+            }
+            offer_lanes(m1, c1, R);
+            offer_lanes(m2, c2, R);
+        }
+    }
+    if (v1 && lane < R) rows[(int64_t)g1 * R + lane] = m1;
+    if (v2 && lane < R) rows[(int64_t)g2 * R + lane] = m2;
+}
+
 // one warp per point: offer the rows of its neighbours (from rin) to its row
 __global__ void __launch_bounds__(PROP_THREADS) rp_prop_kernel(const uint8_t *__restrict__ X, int64_t N, int d, int R,
                                                                const uint64_t *__restrict__ rin,
@@ -223,6 +325,7 @@ int bit_length(uint64_t v) {
 }  // namespace
 
 size_t knn_approx_leaf_smem(int64_t leaf_rows, int d) { return (size_t)leaf_rows * (size_t)(d + 16 + 4); }
+size_t knn_approx_tile_smem(int d) { return (size_t)TILE_J * (size_t)(d + 16 + 8); }
 
 }  // namespace ann
 
@@ -247,8 +350,13 @@ extern "C" int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N
     int dev = 0, optin = 0;
     ANN_CUDA(cudaGetDevice(&dev));
     ANN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const size_t smem = knn_approx_leaf_smem(largest, d);
-    ANN_ARG(smem <= (size_t)optin, "the largest leaf does not fit in shared memory: use more levels");
+    // leaves that fit in one CTA's shared memory are staged whole; larger
+    // ones (d <= 128) are streamed through it
+    const bool tiled = knn_approx_leaf_smem(largest, d) > (size_t)optin;
+    ANN_ARG(!tiled || d <= 128, "with d > 128 the largest leaf must fit in shared memory: use more levels");
+    const size_t smem = tiled ? knn_approx_tile_smem(d) : knn_approx_leaf_smem(largest, d);
+    const int chunks = (int)((largest + TILE_I - 1) / TILE_I);
+    ANN_ARG(!tiled || nleaves * chunks < (1ll << 31), "too many leaf chunks for one launch");
     cudaStream_t s = (cudaStream_t)stream;
 
     const uint64_t idmask = (1ull << id_bits) - 1;
@@ -280,7 +388,9 @@ extern "C" int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N
         AP_CUDA(cudaMallocAsync(&temp, temp_bytes, s));
     }
     AP_CUDA(cudaMemsetAsync(ra, 0xff, sizeof(uint64_t) * (size_t)N * R, s));
-    AP_CUDA(cudaFuncSetAttribute(rp_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (tiled) AP_CUDA(cudaFuncSetAttribute(rp_leaf_tiled_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+    else AP_CUDA(cudaFuncSetAttribute(rp_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int64_t nseg = nleaves - 1;
     const unsigned gridN = (unsigned)((N + 255) / 256);
     for (int r = 0; r < rounds; r++) {
@@ -296,8 +406,13 @@ extern "C" int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N
             size_t tb = temp_bytes;
             AP_CUDA(cub::DeviceRadixSort::SortKeys(temp, tb, keys, (int)N, 0, l + proj_bits + id_bits, s));
         }
-        rp_leaf_kernel<<<(unsigned)nleaves, LEAF_THREADS, smem, s>>>(
-            (const uint8_t *)data, N, d, R, levels, levels > 0 ? keys.Current() : nullptr, idmask, ra);
+        const uint64_t *sorted = levels > 0 ? keys.Current() : nullptr;
+        if (tiled)
+            rp_leaf_tiled_kernel<<<(unsigned)(nleaves * chunks), TILE_THREADS, smem, s>>>(
+                (const uint8_t *)data, N, d, R, levels, chunks, sorted, idmask, ra);
+        else
+            rp_leaf_kernel<<<(unsigned)nleaves, LEAF_THREADS, smem, s>>>((const uint8_t *)data, N, d, R, levels,
+                                                                         sorted, idmask, ra);
         AP_CUDA(cudaGetLastError());
     }
     const unsigned gridW = (unsigned)((N * 32 + PROP_THREADS - 1) / PROP_THREADS);

@@ -4,7 +4,8 @@ Sec. 5.3 uses for its graphs) with the oracle, through the C ABI.
 
 uint8 keys are exact integers, so ids and keys must match bit for bit:
 whole graphs at sizes the oracle finishes in seconds (several leaves, ragged
-leaf sizes, R up to 20, d from 16 to 512, 0 to 2 propagation steps), and
+leaf sizes, R up to 32, d from 16 to 512, 0 to 2 propagation steps, leaves
+staged whole and leaves streamed through shared memory), and
 sampled rows at the full 1M size of the SIFT-shaped workload, which the
 oracle evaluates on demand."""
 from __future__ import annotations
@@ -45,6 +46,9 @@ CASES = [
     (4, 97, 16, 4, 5, 2, 13, 2),
     (5, 3001, 512, 20, 12, 2, 380, 1),
     (6, 4096, 32, 16, 32, 2, 512, 1),
+    # leaves beyond one CTA's shared memory: streamed through it (d <= 128)
+    (7, 9001, 128, 8, 16, 1, 5000, 1),
+    (8, 6000, 64, 6, 10, 2, 3000, 2),
 ]
 
 
@@ -60,8 +64,10 @@ def test_graph_matches_oracle(ann, case):
     assert np.array_equal(gk.astype(np.float64), ok)
 
 
-def test_one_leaf_is_the_exact_graph(ann):
-    X = datagen.mixture(7, 1200, 128, 10, np.uint8)
+@pytest.mark.parametrize("N", [1200, 6007])
+def test_one_leaf_is_the_exact_graph(ann, N):
+    # 1,200 rows fit in shared memory; 6,007 rows are streamed through it
+    X = datagen.mixture(7, N, 128, 10, np.uint8)
     dirs = datagen.rp_directions(7, 1, 0, 128)
     gi, gk = gpu_graph(ann, X, 20, dirs, 1)
     ei, ek = ann.ann_build_knn_graph(torch.from_numpy(X).cuda(), 20)
@@ -76,8 +82,9 @@ def test_deterministic_and_argument_checks(ann):
     b = gpu_graph(ann, X, 16, dirs, 1)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
     Xd = torch.from_numpy(X).cuda()
-    with pytest.raises(ann.AnnError):  # largest leaf (8000 rows) exceeds shared memory
-        ann.ann_build_knn_graph_approx(Xd, 16, torch.from_numpy(datagen.rp_directions(8, 1, 0, 128)).cuda(), 0)
+    Xw = torch.from_numpy(datagen.mixture(9, 3000, 256, 4, np.uint8)).cuda()
+    with pytest.raises(ann.AnnError):  # d > 128 and a leaf of 3,000 rows beyond shared memory
+        ann.ann_build_knn_graph_approx(Xw, 16, torch.from_numpy(datagen.rp_directions(8, 1, 0, 256)).cuda(), 0)
     with pytest.raises(ann.AnnError):  # leaves of 7-8 points cannot fill R = 16
         ann.ann_build_knn_graph_approx(Xd, 16, torch.from_numpy(datagen.rp_directions(8, 1, 10, 128)).cuda(), 0)
     with pytest.raises(ann.AnnError):  # float32 data
