@@ -18,6 +18,10 @@ Functions and the passages they follow:
                  neighbourhood-graph construction (recursive median splits)
   knn_graph_approx  the same reading: leaf brute force over random partitions,
                  then neighbourhood propagation (rows on demand)
+  ivf_lists, pq_encode, adc_rerank, graph_d_adc_search
+                 Sec. 5.4 (Graph-D-ADC): inverted lists under coarse centers,
+                 product-quantized residuals, lists found by Algorithm 1 over
+                 the centers, asymmetric-distance re-ranking
 Every function is pinned by the ``-m "not gpu"`` tests in ``tests/``.
 """
 from __future__ import annotations
@@ -73,6 +77,10 @@ def _load():
                                           i64, P, P, i32, P, P, P, P, i32, i32]
             lib.oracle_search.restype = i32
             lib.oracle_num_stats.restype = i32
+            lib.oracle_pq_encode.argtypes = [P, i64, i32, i32, i32, P, P]
+            lib.oracle_pq_encode.restype = None
+            lib.oracle_adc_rerank.argtypes = [P, i32, P, i32, P, P, P, P, i32, i32, P, i64, i32, P, P]
+            lib.oracle_adc_rerank.restype = i64
             lib.oracle_rp_partition.argtypes = [P, i64, i32, P, i32, P]
             lib.oracle_rp_partition.restype = None
             lib.oracle_knn_graph_approx.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P]
@@ -311,3 +319,66 @@ def knn_graph_approx(X: np.ndarray, R: int, dirs: np.ndarray, iters: int, rows=N
     lib.oracle_knn_graph_approx(_ptr(X), X.shape[0], X.shape[1], R, _ptr(dirs), rounds, levels, iters,
                                 None if sel is None else _ptr(sel), nrows, _ptr(ids), _ptr(keys))
     return ids, keys
+
+
+def ivf_lists(assign: np.ndarray, K: int):
+    """Inverted lists of the coarse quantizer: offsets (K + 1) and members,
+    each list ascending by reference id."""
+    assign = np.asarray(assign, np.int64)
+    assert assign.min() >= 0 and assign.max() < K
+    members = np.argsort(assign, kind="stable").astype(np.int32)
+    offsets = np.zeros(K + 1, np.int64)
+    offsets[1:] = np.cumsum(np.bincount(assign, minlength=K))
+    return offsets, members
+
+
+def pq_encode(R: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
+    """Product-quantization codes of residual rows R (N, d): for each of the
+    m parts the nearest of its ks codewords, ties to the lower index.
+    codebooks: (m, ks, d / m).  Returns (N, m) uint8."""
+    lib = _load()
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    cb = np.ascontiguousarray(codebooks, dtype=np.float64)
+    m, ks, dp = cb.shape
+    N, d = R.shape
+    assert m * dp == d and ks <= 256
+    codes = np.empty((N, m), np.uint8)
+    lib.oracle_pq_encode(_ptr(R), N, d, m, ks, _ptr(cb), _ptr(codes))
+    return codes
+
+
+def adc_rerank(queries: np.ndarray, lists: np.ndarray, offsets: np.ndarray, members: np.ndarray,
+               centers: np.ndarray, codes: np.ndarray, codebooks: np.ndarray, L: int, T: int):
+    """Asymmetric-distance re-ranking: for query i, the first L members of
+    the lists lists[i] (visited in that order; -1 entries skipped) ranked by
+    ||q - c - r^||^2.  Returns (ids (nq, T), keys (nq, T), examined (nq,))."""
+    lib = _load()
+    Qd = np.ascontiguousarray(queries, dtype=np.float64)
+    lists = np.ascontiguousarray(lists, dtype=np.int32)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    members = np.ascontiguousarray(members, dtype=np.int32)
+    Cd = np.ascontiguousarray(centers, dtype=np.float64)
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    cb = np.ascontiguousarray(codebooks, dtype=np.float64)
+    m, ks, _ = cb.shape
+    nq, d = Qd.shape
+    ids = np.empty((nq, T), np.int32)
+    keys = np.empty((nq, T), np.float64)
+    seen = np.empty(nq, np.int64)
+    for i in range(nq):
+        li = np.ascontiguousarray(lists[i])
+        seen[i] = lib.oracle_adc_rerank(_ptr(Qd[i]), d, _ptr(li), len(li), _ptr(offsets), _ptr(members),
+                                        _ptr(Cd), _ptr(codes), m, ks, _ptr(cb), L, T,
+                                        ids[i:].ctypes.data_as(ctypes.c_void_p),
+                                        keys[i:].ctypes.data_as(ctypes.c_void_p))
+    return ids, keys, seen
+
+
+def graph_d_adc_search(coarse: np.ndarray, coarse_graph, part_centers: np.ndarray, bg: dict,
+                       offsets: np.ndarray, members: np.ndarray, codes: np.ndarray, codebooks: np.ndarray,
+                       queries: np.ndarray, w: int, Tc: int, L: int, T: int):
+    """Graph-D-ADC search (Sec. 5.4): Algorithm 1 over the index of the coarse
+    centers (k = w lists, budget Tc), then asymmetric-distance re-ranking of
+    the first L members of those lists.  Returns (ids, keys, examined)."""
+    lists, _, _ = search(coarse, coarse_graph, part_centers, bg, queries, w, Tc)
+    return adc_rerank(queries, lists, offsets, members, coarse, codes, codebooks, L, T)

@@ -1122,3 +1122,89 @@ void oracle_knn_graph_approx(const uint8_t *X, int64_t N, int d, int R, const in
     free(g.perm);
     free(g.pos);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Graph-D-ADC (Sec. 5.4): the method as the coarse quantizer of an inverted */
+/* file with product-quantized residuals.  Each reference x is listed under  */
+/* its assigned coarse center c(x); its residual r = x - c(x) is encoded by  */
+/* m sub-quantizers of ks codewords over contiguous parts of d / m dims.    */
+/* A query visits the lists of its nearest centers (found by Alg. 1 over an */
+/* index of the centers) and re-ranks their members by the asymmetric       */
+/* distance ||q - c - r^||^2, r^ the concatenated codewords of x's code.    */
+/* Readings fixed here: codes take the nearest codeword of each part, ties  */
+/* to the lower codeword index; lists are visited in the order given        */
+/* (ascending coarse key), members of a list ascending by id, and the first */
+/* L members overall are the candidates; the top T candidates by (ADC key, */
+/* id) are returned.  All arithmetic in fp64.                               */
+/* ------------------------------------------------------------------------ */
+
+/* codes[i*m + j] = the codeword of part j nearest to R[i] restricted to the
+   part (R: N*d residuals; codebooks: m*ks*(d/m)). */
+void oracle_pq_encode(const double *R, int64_t N, int d, int m, int ks, const double *codebooks,
+                      uint8_t *codes) {
+    const int dp = d / m;
+    for (int64_t i = 0; i < N; i++) {
+        for (int j = 0; j < m; j++) {
+            const double *r = R + i * d + (int64_t)j * dp;
+            double best = INFINITY;
+            int arg = 0;
+            for (int c = 0; c < ks; c++) {
+                const double *w = codebooks + ((int64_t)j * ks + c) * dp;
+                double s = 0.0;
+                for (int t = 0; t < dp; t++) {
+                    double e = r[t] - w[t];
+                    s += e * e;
+                }
+                if (s < best) {
+                    best = s;
+                    arg = c;
+                }
+            }
+            codes[i * m + j] = (uint8_t)arg;
+        }
+    }
+}
+
+/* Re-rank one query.  lists: the nlists coarse centers to visit, in order;
+   offsets/members: inverted lists (members ascending by id within a list);
+   centers: K*d coarse centers.  Out: the T best (key, id), padded -1/+inf.
+   Returns the number of candidates examined (<= L). */
+int64_t oracle_adc_rerank(const double *q, int d, const int32_t *lists, int nlists, const int64_t *offsets,
+                          const int32_t *members, const double *centers, const uint8_t *codes, int m, int ks,
+                          const double *codebooks, int64_t L, int T, int32_t *out_ids, double *out_keys) {
+    const int dp = d / m;
+    double *table = (double *)malloc(sizeof(double) * (size_t)m * (size_t)ks);
+    double *keys = (double *)malloc(sizeof(double) * (size_t)T);
+    int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)T);
+    int len = 0;
+    int64_t seen = 0;
+    for (int li = 0; li < nlists && seen < L; li++) {
+        const int32_t c = lists[li];
+        if (c < 0) continue;
+        /* table[j][k] = || (q - c)^j - codeword(j, k) ||^2 */
+        for (int j = 0; j < m; j++)
+            for (int k = 0; k < ks; k++) {
+                const double *w = codebooks + ((int64_t)j * ks + k) * dp;
+                double s = 0.0;
+                for (int t = 0; t < dp; t++) {
+                    double e = q[j * dp + t] - centers[(int64_t)c * d + j * dp + t] - w[t];
+                    s += e * e;
+                }
+                table[j * ks + k] = s;
+            }
+        for (int64_t p = offsets[c]; p < offsets[c + 1] && seen < L; p++, seen++) {
+            const int32_t x = members[p];
+            double key = 0.0;
+            for (int j = 0; j < m; j++) key += table[j * ks + codes[(int64_t)x * m + j]];
+            topk_insert(keys, ids, &len, T, key, x);
+        }
+    }
+    for (int r = 0; r < T; r++) {
+        out_ids[r] = r < len ? (int32_t)ids[r] : -1;
+        out_keys[r] = r < len ? keys[r] : INFINITY;
+    }
+    free(table);
+    free(keys);
+    free(ids);
+    return seen;
+}
