@@ -77,7 +77,7 @@ def _load():
                                           i64, P, P, i32, P, P, P, P, i32, i32]
             lib.oracle_search.restype = i32
             lib.oracle_num_stats.restype = i32
-            lib.oracle_pq_encode.argtypes = [P, i64, i32, i32, i32, P, P]
+            lib.oracle_pq_encode.argtypes = [P, i64, i32, P, P, i32, i32, P, P]
             lib.oracle_pq_encode.restype = None
             lib.oracle_adc_rerank.argtypes = [P, i32, P, i32, P, P, P, P, i32, i32, P, i64, i32, P, P]
             lib.oracle_adc_rerank.restype = i64
@@ -332,18 +332,21 @@ def ivf_lists(assign: np.ndarray, K: int):
     return offsets, members
 
 
-def pq_encode(R: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
-    """Product-quantization codes of residual rows R (N, d): for each of the
-    m parts the nearest of its ks codewords, ties to the lower index.
+def pq_encode(X: np.ndarray, centers: np.ndarray, assign: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
+    """Product-quantization codes of the residuals X[i] - centers[assign[i]]:
+    for each of the m parts the nearest of its ks codewords, ties to the
+    lower index, decided in float32 (order fixed in oracle.c).
     codebooks: (m, ks, d / m).  Returns (N, m) uint8."""
     lib = _load()
-    R = np.ascontiguousarray(R, dtype=np.float64)
-    cb = np.ascontiguousarray(codebooks, dtype=np.float64)
+    Xf = np.ascontiguousarray(X, dtype=np.float32)
+    Cf = np.ascontiguousarray(centers, dtype=np.float32)
+    assign = np.ascontiguousarray(assign, dtype=np.int32)
+    cb = np.ascontiguousarray(codebooks, dtype=np.float32)
     m, ks, dp = cb.shape
-    N, d = R.shape
-    assert m * dp == d and ks <= 256
+    N, d = Xf.shape
+    assert m * dp == d and ks <= 256 and assign.shape == (N,)
     codes = np.empty((N, m), np.uint8)
-    lib.oracle_pq_encode(_ptr(R), N, d, m, ks, _ptr(cb), _ptr(codes))
+    lib.oracle_pq_encode(_ptr(Xf), N, d, _ptr(Cf), _ptr(assign), m, ks, _ptr(cb), _ptr(codes))
     return codes
 
 
@@ -351,15 +354,17 @@ def adc_rerank(queries: np.ndarray, lists: np.ndarray, offsets: np.ndarray, memb
                centers: np.ndarray, codes: np.ndarray, codebooks: np.ndarray, L: int, T: int):
     """Asymmetric-distance re-ranking: for query i, the first L members of
     the lists lists[i] (visited in that order; -1 entries skipped) ranked by
-    ||q - c - r^||^2.  Returns (ids (nq, T), keys (nq, T), examined (nq,))."""
+    ||q - c - r^||^2 in float32 (tables and sums in the order fixed in
+    oracle.c).  Returns (ids (nq, T), keys (nq, T) float32 values as float64,
+    examined (nq,))."""
     lib = _load()
-    Qd = np.ascontiguousarray(queries, dtype=np.float64)
+    Qd = np.ascontiguousarray(queries, dtype=np.float32)
     lists = np.ascontiguousarray(lists, dtype=np.int32)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
     members = np.ascontiguousarray(members, dtype=np.int32)
-    Cd = np.ascontiguousarray(centers, dtype=np.float64)
+    Cd = np.ascontiguousarray(centers, dtype=np.float32)
     codes = np.ascontiguousarray(codes, dtype=np.uint8)
-    cb = np.ascontiguousarray(codebooks, dtype=np.float64)
+    cb = np.ascontiguousarray(codebooks, dtype=np.float32)
     m, ks, _ = cb.shape
     nq, d = Qd.shape
     ids = np.empty((nq, T), np.int32)

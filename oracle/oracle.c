@@ -1135,29 +1135,37 @@ void oracle_knn_graph_approx(const uint8_t *X, int64_t N, int d, int R, const in
 /* to the lower codeword index; lists are visited in the order given        */
 /* (ascending coarse key), members of a list ascending by id, and the first */
 /* L members overall are the candidates; the top T candidates by (ADC key, */
-/* id) are returned.  All arithmetic in fp64.                               */
+/* id) are returned.                                                        */
+/* Precision: the paper fixes none; codes and ranks are decided in float32, */
+/* the precision of the lookup tables of asymmetric distance computation,   */
+/* with every operation rounded (no fused multiply-add) in this order:      */
+/* r_t = x_t - c_t; e = r_t - w_t; a part's sum adds e * e for t ascending; */
+/* a table entry uses e = (q_t - c_t) - w_t the same way; a key adds the m  */
+/* table entries for parts ascending.                                       */
 /* ------------------------------------------------------------------------ */
 
-/* codes[i*m + j] = the codeword of part j nearest to R[i] restricted to the
-   part (R: N*d residuals; codebooks: m*ks*(d/m)). */
-void oracle_pq_encode(const double *R, int64_t N, int d, int m, int ks, const double *codebooks,
-                      uint8_t *codes) {
+/* codes[i*m + j] = the codeword of part j nearest to the residual of X[i]
+   (X: N*d, centers: K*d, assign: N coarse ids, codebooks: m*ks*(d/m)). */
+void oracle_pq_encode(const float *X, int64_t N, int d, const float *centers, const int32_t *assign, int m, int ks,
+                      const float *codebooks, uint8_t *codes) {
     const int dp = d / m;
     for (int64_t i = 0; i < N; i++) {
+        const float *x = X + i * d;
+        const float *c = centers + (int64_t)assign[i] * d;
         for (int j = 0; j < m; j++) {
-            const double *r = R + i * d + (int64_t)j * dp;
-            double best = INFINITY;
+            float best = INFINITY;
             int arg = 0;
-            for (int c = 0; c < ks; c++) {
-                const double *w = codebooks + ((int64_t)j * ks + c) * dp;
-                double s = 0.0;
+            for (int k = 0; k < ks; k++) {
+                const float *w = codebooks + ((int64_t)j * ks + k) * dp;
+                float sum = 0.0f;
                 for (int t = 0; t < dp; t++) {
-                    double e = r[t] - w[t];
-                    s += e * e;
+                    float r = x[j * dp + t] - c[j * dp + t];
+                    float e = r - w[t];
+                    sum = sum + e * e;
                 }
-                if (s < best) {
-                    best = s;
-                    arg = c;
+                if (sum < best) {
+                    best = sum;
+                    arg = k;
                 }
             }
             codes[i * m + j] = (uint8_t)arg;
@@ -1165,15 +1173,16 @@ void oracle_pq_encode(const double *R, int64_t N, int d, int m, int ks, const do
     }
 }
 
-/* Re-rank one query.  lists: the nlists coarse centers to visit, in order;
-   offsets/members: inverted lists (members ascending by id within a list);
-   centers: K*d coarse centers.  Out: the T best (key, id), padded -1/+inf.
-   Returns the number of candidates examined (<= L). */
-int64_t oracle_adc_rerank(const double *q, int d, const int32_t *lists, int nlists, const int64_t *offsets,
-                          const int32_t *members, const double *centers, const uint8_t *codes, int m, int ks,
-                          const double *codebooks, int64_t L, int T, int32_t *out_ids, double *out_keys) {
+/* Re-rank one query.  lists: the nlists coarse centers to visit, in order
+   (negative entries skipped); offsets/members: inverted lists (members
+   ascending by id within a list); centers: K*d coarse centers.  Out: the T
+   best (key, id), padded -1/+inf.  Returns the number of candidates
+   examined (<= L). */
+int64_t oracle_adc_rerank(const float *q, int d, const int32_t *lists, int nlists, const int64_t *offsets,
+                          const int32_t *members, const float *centers, const uint8_t *codes, int m, int ks,
+                          const float *codebooks, int64_t L, int T, int32_t *out_ids, double *out_keys) {
     const int dp = d / m;
-    double *table = (double *)malloc(sizeof(double) * (size_t)m * (size_t)ks);
+    float *table = (float *)malloc(sizeof(float) * (size_t)m * (size_t)ks);
     double *keys = (double *)malloc(sizeof(double) * (size_t)T);
     int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)T);
     int len = 0;
@@ -1181,22 +1190,24 @@ int64_t oracle_adc_rerank(const double *q, int d, const int32_t *lists, int nlis
     for (int li = 0; li < nlists && seen < L; li++) {
         const int32_t c = lists[li];
         if (c < 0) continue;
+        const float *cv = centers + (int64_t)c * d;
         /* table[j][k] = || (q - c)^j - codeword(j, k) ||^2 */
         for (int j = 0; j < m; j++)
             for (int k = 0; k < ks; k++) {
-                const double *w = codebooks + ((int64_t)j * ks + k) * dp;
-                double s = 0.0;
+                const float *w = codebooks + ((int64_t)j * ks + k) * dp;
+                float sum = 0.0f;
                 for (int t = 0; t < dp; t++) {
-                    double e = q[j * dp + t] - centers[(int64_t)c * d + j * dp + t] - w[t];
-                    s += e * e;
+                    float r = q[j * dp + t] - cv[j * dp + t];
+                    float e = r - w[t];
+                    sum = sum + e * e;
                 }
-                table[j * ks + k] = s;
+                table[j * ks + k] = sum;
             }
         for (int64_t p = offsets[c]; p < offsets[c + 1] && seen < L; p++, seen++) {
             const int32_t x = members[p];
-            double key = 0.0;
-            for (int j = 0; j < m; j++) key += table[j * ks + codes[(int64_t)x * m + j]];
-            topk_insert(keys, ids, &len, T, key, x);
+            float key = 0.0f;
+            for (int j = 0; j < m; j++) key = key + table[j * ks + codes[(int64_t)x * m + j]];
+            topk_insert(keys, ids, &len, T, (double)key, x);
         }
     }
     for (int r = 0; r < T; r++) {

@@ -3,7 +3,8 @@ coarse quantizer of an inverted file whose residuals are product-quantized,
 re-ranked by asymmetric distance).
 
 The cases use integer data, integer coarse centers and integer codewords, so
-every key is an exact integer in fp64 and every comparison below is exact.
+every key is an exact integer, in the oracle's float32 as in numpy's fp64,
+and every comparison below is exact.
 Each check uses something other than the oracle itself: explicit
 reconstruction of the encoded vectors, a codebook that reproduces every
 residual (asymmetric distance = true distance, so the result is the exact
@@ -26,7 +27,7 @@ def setup(N=800, d=16, K=12, m=4, ks=16, vmax=255, seed=3):
     R = X.astype(np.float64) - C[assign].astype(np.float64)
     init = rng.choice(N, ks, replace=False)
     cb = np.rint(oracle.kmeans(R.astype(np.float32), m, ks, 4, init))   # integer codewords
-    codes = oracle.pq_encode(R, cb)
+    codes = oracle.pq_encode(X, C, assign, cb)
     offsets, members = oracle.ivf_lists(assign, K)
     return X, C, assign, R, cb, codes, offsets, members
 
@@ -44,10 +45,13 @@ def top_t(keys, ids, T):
 
 def test_pq_encode_is_the_nearest_codeword_with_ties_to_the_lower_index():
     rng = np.random.default_rng(1)
-    R = rng.integers(-20, 21, size=(300, 12)).astype(np.float64)
+    X = rng.integers(0, 41, size=(300, 12)).astype(np.float32)
+    C = rng.integers(0, 41, size=(5, 12)).astype(np.float32)
+    assign = rng.integers(0, 5, size=300)
+    R = X.astype(np.float64) - C[assign]
     cb = rng.integers(-20, 21, size=(3, 10, 4)).astype(np.float64)
     cb[1, 7] = cb[1, 3]          # a duplicated codeword: code 3 must win
-    codes = oracle.pq_encode(R, cb)
+    codes = oracle.pq_encode(X, C, assign, cb)
     for j in range(3):
         dist = ((R[:, None, 4 * j:4 * j + 4] - cb[j][None]) ** 2).sum(-1)
         assert np.array_equal(codes[:, j], dist.argmin(axis=1))   # argmin takes the first minimum
@@ -86,7 +90,7 @@ def test_a_codebook_holding_every_residual_gives_the_exact_nearest_neighbours():
     d, K = 8, 10
     X, C, assign, R, _, _, offsets, members = setup(N=700, d=d, K=K, vmax=127, seed=5)
     cb = np.tile(np.concatenate([np.arange(-127, 128), [128]]).astype(np.float64)[None, :, None], (d, 1, 1))
-    codes = oracle.pq_encode(R, cb)
+    codes = oracle.pq_encode(X, C, assign, cb)
     assert np.array_equal(reconstruct(C, assign, cb, codes), X.astype(np.float64))
     Q = datagen.mixture(6, 9, d, 4, np.uint8).astype(np.float32)
     lists = np.tile(np.arange(K, dtype=np.int32), (len(Q), 1))
