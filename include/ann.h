@@ -123,6 +123,40 @@ int ann_build_knn_graph_approx(const void *data, int dtype, int64_t N, int32_t d
                                const int8_t *dirs, int32_t rounds, int32_t levels, int32_t iters,
                                int32_t *out_ids, void *out_keys, void *stream);
 
+/* Graph-D-ADC (Sec. 5.4): the method as the coarse quantizer of an inverted
+ * file whose residuals are product-quantized.  Precision: the paper fixes
+ * none; codes and keys are decided in float32, every operation rounded (no
+ * fused multiply-add), in this order: r_t = x_t - c_t; e = r_t - w_t; a
+ * part's sum adds e * e for t ascending; a key adds the m parts ascending.
+ *
+ * ann_pq_encode: codes[i*m + j] = the codeword of part j (dims
+ * [j*d/m, (j+1)*d/m)) nearest to the residual data[i] - centers[assign[i]],
+ * ties to the lower codeword index.  data: device N*d elements of dtype;
+ * centers: device float32 K*d coarse centers; assign: device int32[N], each
+ * in [0, K) (an entry outside gets code 0); codebooks: device float32
+ * m*ks*(d/m); codes: device uint8[N*m].  Limits: d % m == 0, d/m <= 32,
+ * ks <= 256.  Asynchronous. */
+int ann_pq_encode(const void *data, int dtype, int64_t N, int32_t d, const float *centers, int64_t K,
+                  const int32_t *assign, int32_t m, int32_t ks, const float *codebooks, uint8_t *codes,
+                  void *stream);
+
+/* ann_adc_rerank: for each query q (device float32 nq*d), visit the lists
+ * lists[q*w .. q*w + w) in that order (entries outside [0, K) are skipped),
+ * members of list c being members[offsets[c] .. offsets[c+1]) (device;
+ * offsets int64[K+1]; each list ascending by id); the first L members
+ * overall are the candidates, keyed by the asymmetric distance
+ * ||q - c - r^||^2 = sum over parts j of table_j[code_j], table_j[k] =
+ * ||(q - c)^j - codeword(j, k)||^2.  out_ids: device int32[nq*T], the T
+ * smallest (key, id) ascending, padded with -1; out_keys: device
+ * float32[nq*T] or NULL (+inf padding); out_seen: device int64[nq] or NULL,
+ * the candidates examined (min(L, members of the visited lists)).  Limits:
+ * T <= 128, m <= 64, ks <= 256, m*ks*4 + 16384 bytes of shared memory.
+ * Asynchronous. */
+int ann_adc_rerank(const float *queries, int64_t nq, int32_t d, const int32_t *lists, int32_t w,
+                   const int64_t *offsets, int64_t K, const int32_t *members, const float *centers,
+                   const uint8_t *codes, int32_t m, int32_t ks, const float *codebooks, int64_t L, int32_t T,
+                   int32_t *out_ids, float *out_keys, int64_t *out_seen, void *stream);
+
 /* Per-part dictionaries for the bridge vectors (Sec. 4.1, "Computing bridge
  * vectors": product quantization, i.e. k-means on each of the P contiguous
  * parts of d/P dims).  Lloyd's algorithm in fp64: center j of every part

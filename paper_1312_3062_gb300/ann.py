@@ -56,6 +56,8 @@ _sig("ann_exact_knn", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_
 _sig("ann_exact_knn_static", [P_, i64, P_, i64, ctypes.c_int, i32, i32, i32, P_, P_, P_])
 _sig("ann_build_knn_graph", [P_, ctypes.c_int, i64, i32, i32, P_, P_, P_])
 _sig("ann_build_knn_graph_approx", [P_, ctypes.c_int, i64, i32, i32, P_, i32, i32, i32, P_, P_, P_])
+_sig("ann_pq_encode", [P_, ctypes.c_int, i64, i32, P_, i64, P_, i32, i32, P_, P_, P_])
+_sig("ann_adc_rerank", [P_, i64, i32, P_, i32, P_, i64, P_, P_, P_, i32, i32, P_, i64, i32, P_, P_, P_, P_])
 _sig("ann_train_centers", [P_, ctypes.c_int, i64, i32, i32, i32, i32, P_, P_, P_, P_])
 _sig("ann_index_create", [ctypes.POINTER(ann_index_desc), ctypes.POINTER(P_)])
 _sig("ann_index_load", [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(P_)])
@@ -73,7 +75,7 @@ _sig("ann_serve_latency", [P_, u64], f64)
 _sig("ann_serve_replay", [P_, P_, P_, P_, i32, P_, P_, P_, P_, P_])
 
 EXPORTED = ("ann_last_error", "ann_exact_knn", "ann_exact_knn_static", "ann_build_knn_graph", "ann_build_knn_graph_approx",
-            "ann_train_centers", "ann_index_create",
+            "ann_pq_encode", "ann_adc_rerank", "ann_train_centers", "ann_index_create",
             "ann_index_load", "ann_index_save", "ann_index_free", "ann_index_get_info", "ann_index_get_bridges", "ann_index_lookup_bridges",
             "ann_search_batch", "ann_server_create", "ann_server_destroy", "ann_serve_submit", "ann_serve_poll",
             "ann_serve_latency", "ann_serve_replay")
@@ -165,6 +167,33 @@ def ann_build_knn_graph_approx(data, R, dirs, iters, out_ids=None, out_keys=None
     check(lib.ann_build_knn_graph_approx(ptr(data), dtype_code(data), N, d, R, ptr(dirs) if nseg else None,
                                          rounds, levels, iters, ptr(out_ids), ptr(out_keys), stream_ptr(stream)))
     return out_ids, out_keys
+
+
+def ann_pq_encode(data, centers, assign, codebooks, out=None, stream=None):
+    """codebooks: device float32 (m, ks, d / m); returns device uint8 (N, m)."""
+    import torch
+    N, d = data.shape
+    m, ks, _ = codebooks.shape
+    if out is None:
+        out = torch.empty((N, m), dtype=torch.uint8, device=data.device)
+    check(lib.ann_pq_encode(ptr(data), dtype_code(data), N, d, ptr(centers), centers.shape[0], ptr(assign), m, ks,
+                            ptr(codebooks), ptr(out), stream_ptr(stream)))
+    return out
+
+
+def ann_adc_rerank(queries, lists, offsets, members, centers, codes, codebooks, L, T, stream=None):
+    """lists: device int32 (nq, w); returns (ids int32 (nq, T), keys float32 (nq, T), seen int64 (nq,))."""
+    import torch
+    nq, d = queries.shape
+    w = lists.shape[1]
+    m, ks, _ = codebooks.shape
+    ids = torch.empty((nq, T), dtype=torch.int32, device=queries.device)
+    keys = torch.empty((nq, T), dtype=torch.float32, device=queries.device)
+    seen = torch.empty((nq,), dtype=torch.int64, device=queries.device)
+    check(lib.ann_adc_rerank(ptr(queries), nq, d, ptr(lists), w, ptr(offsets), offsets.shape[0] - 1, ptr(members),
+                             ptr(centers), ptr(codes), m, ks, ptr(codebooks), L, T, ptr(ids), ptr(keys), ptr(seen),
+                             stream_ptr(stream)))
+    return ids, keys, seen
 
 
 def ann_train_centers(train, P, n, iters, init_rows: np.ndarray, want_f64=False, stream=None):
