@@ -136,3 +136,18 @@ def test_more_rounds_and_steps_only_lower_the_keys_and_reach_high_recall(data):
         prev = keys
     recall = np.mean([len(set(ids[i]) & set(gi[i])) / R for i in range(len(X))])
     assert recall >= 0.9, recall
+
+
+def test_input_helpers():
+    # rp_levels: the fewest halvings after which no leaf exceeds leaf_max
+    for N, leaf in ((1, 1), (97, 13), (1000, 1000), (1001, 1000), (10_000_000, 10_000), (1_000_000, 977)):
+        L = datagen.rp_levels(N, leaf)
+        assert -(-N // (1 << L)) <= leaf
+        assert L == 0 or -(-N // (1 << (L - 1))) > leaf
+    # rp_directions: one +-1 direction per segment of every level of every round, seeded
+    dirs = datagen.rp_directions(4, 3, 5, 32)
+    assert dirs.shape == (3, 31, 32) and dirs.dtype == np.int8
+    assert set(np.unique(dirs).tolist()) == {-1, 1}
+    assert np.array_equal(dirs, datagen.rp_directions(4, 3, 5, 32))
+    assert not np.array_equal(dirs, datagen.rp_directions(5, 3, 5, 32))
+    assert datagen.rp_directions(4, 2, 0, 16).shape == (2, 0, 16)
