@@ -151,3 +151,28 @@ def test_input_helpers():
     assert np.array_equal(dirs, datagen.rp_directions(4, 3, 5, 32))
     assert not np.array_equal(dirs, datagen.rp_directions(5, 3, 5, 32))
     assert datagen.rp_directions(4, 2, 0, 16).shape == (2, 0, 16)
+
+
+def test_duplicate_rows_break_ties_by_id():
+    # 300 distinct rows, each five times: many equal keys (0 among copies),
+    # so the id tie-break and the distinct-id rule decide the rows
+    base = datagen.mixture(41, 300, 32, 6, np.uint8)
+    X = np.repeat(base, 5, axis=0)
+    N, R = len(X), 8
+    dirs0 = datagen.rp_directions(43, 1, 0, 32)
+    ids, keys = oracle.knn_graph_approx(X, R, dirs0, 1)
+    gi, gk = oracle.knn_graph(X, R)
+    assert np.array_equal(ids, gi) and np.array_equal(keys, gk)
+    dirs = datagen.rp_directions(43, 2, 4, 32)
+    ids, keys = oracle.knn_graph_approx(X, R, dirs, 0)
+    mates = [set() for _ in range(N)]
+    for r in range(2):
+        perm = oracle.rp_partition(X, dirs[r])
+        for s in range(16):
+            lo, hi = halving(N, 4, s)
+            for i in perm[lo:hi]:
+                mates[i].update(perm[lo:hi].tolist())
+    for i in range(N):
+        ti, tk = top_r(X, i, mates[i], R)
+        assert np.array_equal(ids[i], ti) and np.array_equal(keys[i], tk), i
+        assert len(set(ids[i].tolist())) == R
