@@ -58,3 +58,18 @@ def test_argument_errors_need_no_gpu(libpath):
     for a, msg in cases:
         rc = ann.lib.ann_build_knn_graph_approx(*a, None, None)
         assert rc == ann.ANN_ERR_ARG and msg in ann.lib.ann_last_error(), (a, ann.lib.ann_last_error())
+    # Graph-D-ADC entry points: shapes and limits are checked on the host
+    enc = [((16, ann.ANN_U8, 100, 128, 16, 10, 16, 2, 256, 16, 16, None), b"32 dims per part"),
+           ((16, ann.ANN_U8, 100, 128, 16, 10, 16, 7, 256, 16, 16, None), b"multiple of m"),
+           ((16, ann.ANN_U8, 100, 128, 16, 10, 16, 8, 257, 16, 16, None), b"ks must be"),
+           ((16, 7, 100, 128, 16, 10, 16, 8, 256, 16, 16, None), b"dtype")]
+    for a, msg in enc:
+        rc = ann.lib.ann_pq_encode(*a)
+        assert rc == ann.ANN_ERR_ARG and msg in ann.lib.ann_last_error(), (a, ann.lib.ann_last_error())
+    rr = [((16, 4, 128, 16, 8, 16, 10, 16, 16, 16, 8, 256, 16, 1000, 129, 16, None, None, None), b"T must be"),
+          ((16, 4, 128, 16, 8, 16, 10, 16, 16, 16, 65, 256, 16, 1000, 10, 16, None, None, None), b"m <= 64"),
+          ((16, 4, 128, 16, 0, 16, 10, 16, 16, 16, 8, 256, 16, 1000, 10, 16, None, None, None), b"w >= 1"),
+          ((16, 4, 128, None, 8, 16, 10, 16, 16, 16, 8, 256, 16, 1000, 10, 16, None, None, None), b"null")]
+    for a, msg in rr:
+        rc = ann.lib.ann_adc_rerank(*a)
+        assert rc == ann.ANN_ERR_ARG and msg in ann.lib.ann_last_error(), (a, ann.lib.ann_last_error())
