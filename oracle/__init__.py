@@ -81,6 +81,8 @@ def _load():
             lib.oracle_pq_encode.restype = None
             lib.oracle_adc_rerank.argtypes = [P, i32, P, i32, P, P, P, P, i32, i32, P, i64, i32, P, P]
             lib.oracle_adc_rerank.restype = i64
+            lib.oracle_adc_keys.argtypes = [P, i32, P, i64, P, P, P, i32, i32, P, P]
+            lib.oracle_adc_keys.restype = None
             lib.oracle_rp_partition.argtypes = [P, i64, i32, P, i32, P]
             lib.oracle_rp_partition.restype = None
             lib.oracle_knn_graph_approx.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P]
@@ -334,8 +336,8 @@ def ivf_lists(assign: np.ndarray, K: int):
 
 def pq_encode(X: np.ndarray, centers: np.ndarray, assign: np.ndarray, codebooks: np.ndarray) -> np.ndarray:
     """Product-quantization codes of the residuals X[i] - centers[assign[i]]:
-    for each of the m parts the nearest of its ks codewords, ties to the
-    lower index, decided in float32 (order fixed in oracle.c).
+    for each of the m parts the nearest of its ks codewords (distances in
+    fp64), ties to the lower index.
     codebooks: (m, ks, d / m).  Returns (N, m) uint8."""
     lib = _load()
     Xf = np.ascontiguousarray(X, dtype=np.float32)
@@ -354,9 +356,8 @@ def adc_rerank(queries: np.ndarray, lists: np.ndarray, offsets: np.ndarray, memb
                centers: np.ndarray, codes: np.ndarray, codebooks: np.ndarray, L: int, T: int):
     """Asymmetric-distance re-ranking: for query i, the first L members of
     the lists lists[i] (visited in that order; -1 entries skipped) ranked by
-    ||q - c - r^||^2 in float32 (tables and sums in the order fixed in
-    oracle.c).  Returns (ids (nq, T), keys (nq, T) float32 values as float64,
-    examined (nq,))."""
+    (||q - c - r^||^2 in fp64, id).  Returns (ids (nq, T), keys (nq, T)
+    float64, examined (nq,))."""
     lib = _load()
     Qd = np.ascontiguousarray(queries, dtype=np.float32)
     lists = np.ascontiguousarray(lists, dtype=np.int32)
@@ -377,6 +378,24 @@ def adc_rerank(queries: np.ndarray, lists: np.ndarray, offsets: np.ndarray, memb
                                         ids[i:].ctypes.data_as(ctypes.c_void_p),
                                         keys[i:].ctypes.data_as(ctypes.c_void_p))
     return ids, keys, seen
+
+
+def adc_keys(q: np.ndarray, cand: np.ndarray, assign: np.ndarray, centers: np.ndarray, codes: np.ndarray,
+             codebooks: np.ndarray) -> np.ndarray:
+    """fp64 asymmetric distances ||q - c(x) - r^(x)||^2 of the candidates cand
+    (ids; x is listed under assign[x]) to the one query q."""
+    lib = _load()
+    qd = np.ascontiguousarray(q, dtype=np.float32)
+    cand = np.ascontiguousarray(cand, dtype=np.int32)
+    assign = np.ascontiguousarray(assign, dtype=np.int32)
+    Cd = np.ascontiguousarray(centers, dtype=np.float32)
+    codes = np.ascontiguousarray(codes, dtype=np.uint8)
+    cb = np.ascontiguousarray(codebooks, dtype=np.float32)
+    m, ks, _ = cb.shape
+    out = np.empty(len(cand), np.float64)
+    lib.oracle_adc_keys(_ptr(qd), qd.shape[0], _ptr(cand), len(cand), _ptr(assign), _ptr(Cd), _ptr(codes), m, ks,
+                        _ptr(cb), _ptr(out))
+    return out
 
 
 def graph_d_adc_search(coarse: np.ndarray, coarse_graph, part_centers: np.ndarray, bg: dict,

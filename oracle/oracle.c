@@ -16,8 +16,10 @@
  *  - float32 data: a key is computed in fp64 and then rounded to the nearest
  *    float32; every comparison is taken on that float32 value (the kernel's
  *    precision), so both implementations order candidates identically.
- *    A bridge key is the float32 sum (D0 + D1) + (D2 + D3 + ...) of the part
- *    keys, the second group added left to right.
+ *    A bridge key (Sec. 4.2: the sum over parts of the part distances) is
+ *    the float32 nearest to the EXACT sum of the P float32 part keys, ties
+ *    to even: one rounding, no grouping, and monotone in every part key, so
+ *    the multi-sequence order of Sec. 3.3 holds for it.
  *  - Main queue order: (key, kind, id), kind ref = 0 < bridge = 1.
  *  - Result set: the k smallest by (key, id), returned ascending, padded with
  *    id -1 / key +inf when fewer than k points were discovered.
@@ -40,6 +42,7 @@
 #include <string.h>
 
 enum { DT_U8 = 0, DT_F32 = 1 };
+#define MAXP_KEY 8 /* most parts a bridge key sums */
 
 /* ------------------------------------------------------------------------ */
 /* Distances (Sec. 2: dist(q, x) = ||q - x||_2; Sec. 3.2: squared tables)    */
@@ -71,23 +74,72 @@ static const void *row_ptr(const void *base, int64_t row, int len, int dtype) {
     return (const float *)base + row * (int64_t)len;
 }
 
+/* The float32 nearest to the exact sum of n finite, non-negative float32
+   values, ties to the even significand.  Every such value is an integer
+   multiple of 2^-149 below 2^128, so the sum is held exactly as an integer
+   count of 2^-149 in eleven 32-bit limbs (little end first) and rounded
+   once to 24 significant bits at the end. */
+static float f32_exact_sum(const float *v, int n) {
+    uint32_t acc[11] = {0};
+    for (int i = 0; i < n; i++) {
+        uint32_t bits;
+        memcpy(&bits, &v[i], sizeof bits);
+        uint32_t ex = (bits >> 23) & 0xffu, man = bits & 0x7fffffu;
+        /* normal: (2^23 + man) * 2^(ex - 150) = (2^23 + man) << (ex - 1) units;
+           subnormal (ex = 0): man units */
+        int sh = 0;
+        if (ex) {
+            man |= 0x800000u;
+            sh = (int)ex - 1;
+        }
+        uint64_t part = (uint64_t)man << (sh % 32); /* < 2^55 */
+        uint64_t carry = 0;
+        for (int j = sh / 32; j < 11; j++) {
+            uint64_t add = j == sh / 32 ? (part & 0xffffffffu) : (j == sh / 32 + 1 ? part >> 32 : 0);
+            uint64_t t = (uint64_t)acc[j] + add + carry;
+            acc[j] = (uint32_t)t;
+            carry = t >> 32;
+        }
+    }
+    int top = -1; /* highest set bit */
+    for (int j = 10; j >= 0 && top < 0; j--)
+        for (int b = 31; b >= 0; b--)
+            if ((acc[j] >> b) & 1u) {
+                top = 32 * j + b;
+                break;
+            }
+#define ACC_BIT(pos) ((acc[(pos) / 32] >> ((pos) % 32)) & 1u)
+    if (top < 24) { /* below 2^24 units: exactly representable */
+        uint32_t q = 0;
+        for (int b = top; b >= 0; b--) q = (q << 1) | ACC_BIT(b);
+        return ldexpf((float)q, -149);
+    }
+    int low = top - 23; /* the kept bits are [low, top] */
+    uint32_t q = 0;
+    for (int b = top; b >= low; b--) q = (q << 1) | ACC_BIT(b);
+    uint32_t round = ACC_BIT(low - 1), sticky = 0;
+    for (int b = low - 2; b >= 0 && !sticky; b--) sticky = ACC_BIT(b);
+#undef ACC_BIT
+    if (round && (sticky || (q & 1u))) q++;
+    if (q == (1u << 24)) { /* carried into a new bit */
+        q >>= 1;
+        low++;
+    }
+    return ldexpf((float)q, low - 149);
+}
+
 /* Bridge key from P part keys (Sec. 4.2: dist^2(q, y) = sum_p dist^2(q^p, y^p)).
-   For float32 the sum is taken in float32 with a fixed grouping: the first
-   two parts, plus the remaining parts added left to right, i.e.
-   (D0 + D1) + ((D2 + D3) + ...).  Any fixed grouping is monotone in every
-   part key; this one is fixed here so both implementations round alike. */
+   uint8: the exact integer sum.  float32: the part keys are float32 values
+   and the key is the float32 nearest to their exact sum (one rounding). */
 static double bridge_key(const double *part_keys, int P, int dtype) {
     if (dtype == DT_U8) {
         double s = 0.0; /* integers far below 2^53: exact */
         for (int p = 0; p < P; p++) s += part_keys[p];
         return s;
     } else {
-        if (P == 1) return (double)(float)part_keys[0];
-        float a = (float)part_keys[0] + (float)part_keys[1];
-        if (P == 2) return (double)a;
-        float b = (float)part_keys[2];
-        for (int p = 3; p < P; p++) b = b + (float)part_keys[p];
-        return (double)(a + b);
+        float f[MAXP_KEY];
+        for (int p = 0; p < P; p++) f[p] = (float)part_keys[p];
+        return (double)f32_exact_sum(f, P);
     }
 }
 
@@ -1136,12 +1188,11 @@ void oracle_knn_graph_approx(const uint8_t *X, int64_t N, int d, int R, const in
 /* (ascending coarse key), members of a list ascending by id, and the first */
 /* L members overall are the candidates; the top T candidates by (ADC key, */
 /* id) are returned.                                                        */
-/* Precision: the paper fixes none; codes and ranks are decided in float32, */
-/* the precision of the lookup tables of asymmetric distance computation,   */
-/* with every operation rounded (no fused multiply-add) in this order:      */
-/* r_t = x_t - c_t; e = r_t - w_t; a part's sum adds e * e for t ascending; */
-/* a table entry uses e = (q_t - c_t) - w_t the same way; a key adds the m  */
-/* table entries for parts ascending.                                       */
+/* Precision: the paper fixes none.  Both distances are real-valued        */
+/* squared distances of Sec. 5.4 (nearest codeword; asymmetric distance     */
+/* between the query and the reconstruction c + r^), taken here in fp64 on  */
+/* the float32 inputs, so a code or a rank differs from the real one only   */
+/* where two candidates lie within fp64 rounding of each other.             */
 /* ------------------------------------------------------------------------ */
 
 /* codes[i*m + j] = the codeword of part j nearest to the residual of X[i]
@@ -1153,17 +1204,16 @@ void oracle_pq_encode(const float *X, int64_t N, int d, const float *centers, co
         const float *x = X + i * d;
         const float *c = centers + (int64_t)assign[i] * d;
         for (int j = 0; j < m; j++) {
-            float best = INFINITY;
+            double best = INFINITY;
             int arg = 0;
             for (int k = 0; k < ks; k++) {
                 const float *w = codebooks + ((int64_t)j * ks + k) * dp;
-                float sum = 0.0f;
+                double sum = 0.0;
                 for (int t = 0; t < dp; t++) {
-                    float r = x[j * dp + t] - c[j * dp + t];
-                    float e = r - w[t];
-                    sum = sum + e * e;
+                    double e = ((double)x[j * dp + t] - (double)c[j * dp + t]) - (double)w[t];
+                    sum += e * e;
                 }
-                if (sum < best) {
+                if (sum < best) { /* strict: ties keep the lower codeword */
                     best = sum;
                     arg = k;
                 }
@@ -1171,6 +1221,21 @@ void oracle_pq_encode(const float *X, int64_t N, int d, const float *centers, co
             codes[i * m + j] = (uint8_t)arg;
         }
     }
+}
+
+/* The asymmetric distance of one candidate x listed under center c:
+   sum over parts j of || (q - c)^j - codeword(j, code_j(x)) ||^2. */
+static double adc_key(const float *q, const float *cv, const uint8_t *code, int m, int ks, int dp,
+                      const float *codebooks) {
+    double key = 0.0;
+    for (int j = 0; j < m; j++) {
+        const float *w = codebooks + ((int64_t)j * ks + code[j]) * dp;
+        for (int t = 0; t < dp; t++) {
+            double e = ((double)q[j * dp + t] - (double)cv[j * dp + t]) - (double)w[t];
+            key += e * e;
+        }
+    }
+    return key;
 }
 
 /* Re-rank one query.  lists: the nlists coarse centers to visit, in order
@@ -1182,7 +1247,6 @@ int64_t oracle_adc_rerank(const float *q, int d, const int32_t *lists, int nlist
                           const int32_t *members, const float *centers, const uint8_t *codes, int m, int ks,
                           const float *codebooks, int64_t L, int T, int32_t *out_ids, double *out_keys) {
     const int dp = d / m;
-    float *table = (float *)malloc(sizeof(float) * (size_t)m * (size_t)ks);
     double *keys = (double *)malloc(sizeof(double) * (size_t)T);
     int64_t *ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)T);
     int len = 0;
@@ -1191,31 +1255,28 @@ int64_t oracle_adc_rerank(const float *q, int d, const int32_t *lists, int nlist
         const int32_t c = lists[li];
         if (c < 0) continue;
         const float *cv = centers + (int64_t)c * d;
-        /* table[j][k] = || (q - c)^j - codeword(j, k) ||^2 */
-        for (int j = 0; j < m; j++)
-            for (int k = 0; k < ks; k++) {
-                const float *w = codebooks + ((int64_t)j * ks + k) * dp;
-                float sum = 0.0f;
-                for (int t = 0; t < dp; t++) {
-                    float r = q[j * dp + t] - cv[j * dp + t];
-                    float e = r - w[t];
-                    sum = sum + e * e;
-                }
-                table[j * ks + k] = sum;
-            }
         for (int64_t p = offsets[c]; p < offsets[c + 1] && seen < L; p++, seen++) {
             const int32_t x = members[p];
-            float key = 0.0f;
-            for (int j = 0; j < m; j++) key = key + table[j * ks + codes[(int64_t)x * m + j]];
-            topk_insert(keys, ids, &len, T, (double)key, x);
+            topk_insert(keys, ids, &len, T, adc_key(q, cv, codes + (int64_t)x * m, m, ks, dp, codebooks), x);
         }
     }
     for (int r = 0; r < T; r++) {
         out_ids[r] = r < len ? (int32_t)ids[r] : -1;
         out_keys[r] = r < len ? keys[r] : INFINITY;
     }
-    free(table);
     free(keys);
     free(ids);
     return seen;
+}
+
+/* The asymmetric distances of n given candidates to one query (x's list is
+   assign[x]), for comparing any candidate a caller holds. */
+void oracle_adc_keys(const float *q, int d, const int32_t *cand, int64_t n, const int32_t *assign,
+                     const float *centers, const uint8_t *codes, int m, int ks, const float *codebooks,
+                     double *out_keys) {
+    const int dp = d / m;
+    for (int64_t i = 0; i < n; i++) {
+        const int32_t x = cand[i];
+        out_keys[i] = adc_key(q, centers + (int64_t)assign[x] * d, codes + (int64_t)x * m, m, ks, dp, codebooks);
+    }
 }

@@ -2,9 +2,10 @@
 coarse quantizer of an inverted file whose residuals are product-quantized,
 re-ranked by asymmetric distance).
 
-The cases use integer data, integer coarse centers and integer codewords, so
-every key is an exact integer, in the oracle's float32 as in numpy's fp64,
-and every comparison below is exact.
+Most cases use integer data, integer coarse centers and integer codewords,
+so every key is an exact integer in the oracle's fp64 as in numpy's, and the
+comparisons are exact; one case uses real-valued k-means centers and
+codewords and bounds the fp64 rounding instead.
 Each check uses something other than the oracle itself: explicit
 reconstruction of the encoded vectors, a codebook that reproduces every
 residual (asymmetric distance = true distance, so the result is the exact
@@ -148,3 +149,37 @@ def test_graph_d_adc_search_visits_the_lists_algorithm_1_finds(w):
     near, _ = oracle.exact_knn(C, Q, w)
     sizes = offsets[1:] - offsets[:-1]
     assert np.array_equal(seen, sizes[near].sum(1))
+
+
+def test_real_valued_codes_and_keys_within_fp64_rounding():
+    # real-valued centers and codewords: the oracle's codes are the nearest
+    # codewords of numpy's explicit distances (up to fp64 near-ties) and its
+    # keys the distances to numpy's explicit reconstruction c + r^, within
+    # the rounding of fp64 sums of d terms
+    rng = np.random.default_rng(11)
+    X = datagen.mixture(12, 1500, 32, 8, np.float32)
+    d, K, m, ks = 32, 9, 4, 12
+    C = oracle.kmeans(X, 1, K, 3, rng.choice(len(X), K, replace=False))[0].astype(np.float32)
+    assign, _ = oracle.exact_knn(C, X, 1)
+    assign = assign[:, 0]
+    R = X.astype(np.float64) - C[assign].astype(np.float64)
+    cb = oracle.kmeans(R.astype(np.float32), m, ks, 3, rng.choice(len(X), ks, replace=False)).astype(np.float32)
+    codes = oracle.pq_encode(X, C, assign, cb)
+    dp = d // m
+    for j in range(m):
+        dist = ((R[:, None, j * dp:(j + 1) * dp] - cb[j].astype(np.float64)[None]) ** 2).sum(-1)
+        best = dist.min(1)
+        got = dist[np.arange(len(X)), codes[:, j]]
+        assert np.all(got <= best + 1e-12 * (1 + best))
+    Xr = reconstruct(C, assign, cb.astype(np.float64), codes)
+    offsets, members = oracle.ivf_lists(assign, K)
+    Q = datagen.mixture(13, 5, d, 8, np.float32)
+    lists = np.tile(np.arange(K, dtype=np.int32), (len(Q), 1))
+    ids, keys, _ = oracle.adc_rerank(Q, lists, offsets, members, C, codes, cb, L=len(X), T=40)
+    for i in range(len(Q)):
+        k = ((Xr - Q[i].astype(np.float64)) ** 2).sum(1)
+        order = np.argsort(k, kind="stable")[:40]
+        np.testing.assert_allclose(keys[i], k[order], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(k[ids[i]], keys[i], rtol=1e-12, atol=0)
+        kc = oracle.adc_keys(Q[i], ids[i], assign, C, codes, cb)
+        np.testing.assert_array_equal(kc, keys[i])

@@ -54,18 +54,12 @@ def part_tables(q, centers):
 
 
 def bridge_key_py(parts_keys, dtype):
+    """Sec. 4.2's bridge key, sum_p of the part keys: the exact integer sum for
+    bytes; for float32 the float32 nearest to the exact (rational) sum of the
+    float32 part keys."""
     if np.dtype(dtype) == np.uint8:
         return float(sum(int(v) for v in parts_keys))
-    v = [np.float32(x) for x in parts_keys]
-    if len(v) == 1:
-        return float(v[0])
-    a = np.float32(v[0] + v[1])
-    if len(v) == 2:
-        return float(a)
-    b = v[2]
-    for x in v[3:]:
-        b = np.float32(b + x)
-    return float(np.float32(a + b))
+    return nearest_f32(sum(Fraction(float(np.float32(x))) for x in parts_keys))
 
 
 def all_bridges_sorted(D, dtype):
@@ -241,6 +235,39 @@ def test_multiseq_equals_full_sort(oracle_lib, P, n, dtype):
     assert [e[0] for e in full] == list(keys)
     assert [bridge_id(e[2], n) for e in full] == [int(v) for v in ids]
     assert [e[1] for e in full] == [tuple(r) for r in ranks]
+
+
+def _f32(bits):
+    return float(np.array([bits], np.uint32).view(np.float32)[0])
+
+
+@pytest.mark.parametrize("P", [2, 3, 4])
+def test_f32_bridge_key_is_nearest_float32_of_the_exact_sum(oracle_lib, P):
+    # One center per part: the only bridge's key is the key of the part keys'
+    # sum.  Cases where any grouped float32 sum (or a float64 sum rounded
+    # again) would round differently: halfway cases broken by a tiny term,
+    # exact halfway cases (ties to even), very wide exponent spreads,
+    # subnormals, zeros, and random values.
+    rng = np.random.default_rng(77 + P)
+    eps = 2.0 ** -24
+    cases = [
+        [1.0, eps, 2.0 ** -60, 0.0],          # halfway + tiny: rounds up
+        [1.0, eps, 0.0, 0.0],                 # exact halfway: ties to even (down)
+        [1.0 + 2 * eps, eps, 0.0, 0.0],       # exact halfway, odd significand: up
+        [1.0, 2.0 ** -25, 2.0 ** -25, 2.0 ** -80],  # two quarter-ulps make a half, plus tiny
+        [3.0, 2.0 ** -120, 2.0 ** -149, 2.0 ** -140],
+        [2.0 ** -149, 2.0 ** -149, 2.0 ** -148, 0.0],
+        [0.0, 0.0, 0.0, 0.0],
+        [2.0 ** 100, 1.0, 2.0 ** 76, 2.0 ** 75],
+        [_f32(0x3f7fffff), _f32(0x33000000), _f32(0x2f000000), 0.0],
+    ]
+    for _ in range(300):
+        e = rng.integers(-40, 10, size=4)
+        cases.append([float(np.float32(rng.random() * 2.0 ** int(x))) for x in e])
+    for c in cases:
+        parts = np.array([[np.float32(v)] for v in c[:P]], np.float64)
+        keys, ids, _, _ = oracle.multiseq(parts, np.float32, 1)
+        assert keys[0] == bridge_key_py(parts[:, 0], np.float32), c[:P]
 
 
 def test_multiseq_prefix_and_frontier_bound(oracle_lib):
