@@ -78,13 +78,18 @@ int ann_exact_knn(const void *refs, int64_t N, const void *queries, int64_t nq, 
  * callers that cannot allocate device memory themselves (a host program
  * whose device memory belongs to another allocator, or a latency-critical
  * loop that cannot take an allocation's synchronisation and latency).
- * Limits: for ANN_U8, N plus nq (nq counts only when queries != refs) must
- * not exceed 1048576, otherwise ANN_ERR_CAPACITY; ANN_F32 needs no scratch.
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture.  Every call
- * shares the one array, so calls that overlap on the GPU (other streams,
- * other host threads) race: serialise them.  Nothing in the array needs to
- * start at zero -- each call writes every norm it reads.  Asynchronous. */
+ * Limits: for ANN_U8, N plus nq (nq counts unless the queries are the first
+ * nq rows of refs, i.e. queries == refs and nq <= N) must not exceed
+ * 1048576, otherwise ANN_ERR_CAPACITY; ANN_F32 needs no scratch, but it
+ * always runs the plain SIMT scan: at N >= 8192 and nq >= 256 it is about
+ * 50x slower than ann_exact_knn, whose float32 tensor-core path needs
+ * workspace.  The first call on a device looks up the array's device
+ * address (once per device) and keeps it for the life of the process; make
+ * that first call before any stream capture, and do not call this entry
+ * point on a device after cudaDeviceReset.  Every call shares the one array,
+ * so calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  Nothing in the array needs to start at zero -- each call
+ * writes every norm it reads.  Asynchronous. */
 int ann_exact_knn_static(const void *refs, int64_t N, const void *queries, int64_t nq, int dtype,
                          int32_t d, int32_t k, int32_t exclude_self, int32_t *out_ids,
                          void *out_keys, void *stream);

@@ -12,10 +12,11 @@
 //    merged by a bitonic sort when the buffer fills.  The result, the T
 //    smallest (key, id) of all candidates, does not depend on the order in
 //    which candidates arrive.
-// Codes and keys are decided in float32 with every operation rounded (no
-// fused multiply-add): r = x - c, e = r - w, sums over dims ascending, keys
-// over parts ascending -- so the results are bit-identical to a plain CPU
-// statement that follows the same order.
+// Codes and keys are decided in float32 (the precision of the lookup tables
+// of asymmetric distance computation) with every operation rounded: each
+// distance is within (dp + m + 8) * 2^-24 * sum_t (|a_t| + |w_t|)^2 of the
+// real one (a = x - c or q - c, w the codeword), so a code or a rank differs
+// from the real-valued one of Sec. 5.4 only at near-ties of that size.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -157,8 +158,13 @@ __global__ void __launch_bounds__(RR_THREADS) adc_rerank_kernel(
                 }
             }
             __syncthreads();
-            if (pending > (unsigned)(cap - RR_CHUNK)) {  // uniform: read after the barrier
-                for (int i = T + (int)pending + threadIdx.x; i < RR_SORT; i += blockDim.x) buf[i] = ~0ull;
+            // every thread takes the count of this chunk into a register, and
+            // no thread may add to it for the next chunk before all have read
+            // it, so the merge decision is the same in every thread
+            const unsigned pend = pending;
+            __syncthreads();
+            if (pend > (unsigned)(cap - RR_CHUNK)) {
+                for (int i = T + (int)pend + threadIdx.x; i < RR_SORT; i += blockDim.x) buf[i] = ~0ull;
                 __syncthreads();
                 cta_bitonic_sort(buf);
                 if (threadIdx.x == 0) {

@@ -189,13 +189,9 @@ __global__ void bg_topt_kernel(const void *X, int64_t N, int d, int P, int n, co
                 uint32_t rr = cands[c];
                 uint32_t r[kMaxP];
                 for (int p = 0; p < P; p++) r[p] = (rr >> (8 * (P - 1 - p))) & 255u;
-                uint32_t a = KeyOps<DT>::add(skey[r[0]], skey[n + r[1]]);
-                uint32_t key = a;
-                if (P > 2) {
-                    uint32_t b = skey[2 * n + r[2]];
-                    for (int p = 3; p < P; p++) b = KeyOps<DT>::add(b, skey[p * n + r[p]]);
-                    key = KeyOps<DT>::add(a, b);
-                }
+                // Sec. 4.2: the sum of the part keys (float32: nearest to the exact sum)
+                const uint32_t key = KeyOps<DT>::sum4(skey[r[0]], skey[n + r[1]], P > 2 ? skey[2 * n + r[2]] : 0u,
+                                                      P > 3 ? skey[3 * n + r[3]] : 0u);
                 v = ((uint64_t)key << 32) | rr;
             }
             tmp[c] = v;

@@ -245,7 +245,7 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
     if (dtype == ANN_U8) {
         ANN_CUDA(cudaMallocAsync((void **)&rn, 4 * N, s));
         norms_u8_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((const uint8_t *)refs, N, d, rn);
-        if (queries == refs) {
+        if (queries == refs && nq <= N) {  // the query rows are the first nq reference rows
             qn = rn;
         } else {
             ANN_CUDA(cudaMallocAsync((void **)&qn, 4 * nq, s));
@@ -321,7 +321,9 @@ extern "C" int ann_exact_knn_static(const void *refs, int64_t N, const void *que
             "d must be a multiple of 16 (u8) or 4 (f32)");
     ANN_ARG(refs && (nq == 0 || (queries && out_ids)), "refs, queries and out_ids are required");
     ANN_ARG(!exclude_self || (queries == refs && nq == N), "exclude_self needs queries == refs");
-    const bool shared = queries == refs;
+    // the queries reuse the reference norms only when they are the first nq
+    // reference rows; a longer query buffer at the same address gets its own
+    const bool shared = queries == refs && nq <= N;
     const int64_t rows = dtype == ANN_U8 ? N + (shared ? 0 : nq) : 0;
     if (rows > kStaticNormRows)
         return fail(ANN_ERR_CAPACITY, "ann_exact_knn_static: N (+ nq when queries differ from refs) exceeds the "

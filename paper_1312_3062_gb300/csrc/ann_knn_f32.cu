@@ -285,7 +285,7 @@ int knn_f32_tensor(const float *refs, int64_t N, const float *queries, int64_t n
     // tile of query rows: the tile's dot products take at most 2^31 floats
     int64_t tm = std::max<int64_t>(32, std::min<int64_t>(nq, ((int64_t)1 << 31) / N) / 32 * 32);
     if (tm > nq) tm = nq;
-    const bool shared = queries == refs;
+    const bool shared = queries == refs && nq <= N;  // queries are the first nq reference rows
     __nv_bfloat16 *x3 = nullptr, *q3 = nullptr;
     double *rn64 = nullptr, *qn64 = nullptr;
     float *rn32 = nullptr, *qn32 = nullptr, *D = nullptr, *akth = nullptr;

@@ -469,7 +469,7 @@ int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_
     int dev = 0, nsm = 0;
     ANN_CUDA(cudaGetDevice(&dev));
     ANN_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const bool shared = queries == refs;
+    const bool shared = queries == refs && nq <= N;  // queries are the first nq reference rows
     uint16_t *rb = nullptr, *qb = nullptr;
     uint32_t *rn = nullptr, *qn = nullptr;
     int *derr = nullptr;

@@ -19,7 +19,9 @@
 // All per-query state lives in the warp's slice of shared memory; no device
 // trap or unbounded wait exists on this path.  Keys are squared distances:
 // exact uint32 for uint8 data; for float32 data the float32 nearest to the
-// exact value (double-float accumulation, then one rounding).
+// exact value (double-float accumulation, then one rounding).  A float32
+// bridge key is the float32 nearest to the exact sum of its float32 part
+// keys; the walk skips work only on bounds taken with directed rounding.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -483,16 +485,16 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     for (int r0 = lane; r0 < n; r0 += 32) {
         uint32_t c;
         if (PA == 1) {
-            c = KeyOps<DT>::add(sk(r0), msuf) <= hik ? 1u : 0u;
+            c = KeyOps<DT>::add_lo(sk(r0), msuf) <= hik ? 1u : 0u;
         } else {
             uint32_t a0 = sk(r0);
-            if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk(n)), msuf) > hik) {
+            if (KeyOps<DT>::add_lo(KeyOps<DT>::add_lo(a0, sk(n)), msuf) > hik) {
                 c = 0;
             } else {
                 int lo1 = 1, hi1 = n;  // answer in [1, n]
                 while (lo1 < hi1) {
                     int mid = (lo1 + hi1 + 1) >> 1;
-                    if (KeyOps<DT>::add(KeyOps<DT>::add(a0, sk(n + mid - 1)), msuf) <= hik) lo1 = mid;
+                    if (KeyOps<DT>::add_lo(KeyOps<DT>::add_lo(a0, sk(n + mid - 1)), msuf) <= hik) lo1 = mid;
                     else hi1 = mid - 1;
                 }
                 c = (uint32_t)lo1;
@@ -547,7 +549,7 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
             } else {
                 uint32_t c1 = sc[n + r1];
                 node = c0 * n + c1;
-                kpre = KeyOps<DT>::add(D[c0], D[n + c1]);
+                kpre = KeyOps<DT>::add_lo(D[c0], D[n + c1]);  // a lower bound for float32
                 rpre = ((uint32_t)r0 << 8) | (uint32_t)r1;
             }
             ok = (__ldg(ix.bmA + (node >> 5)) >> (node & 31)) & 1u;
@@ -596,7 +598,7 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                         const uint32_t c2 = __ldg(ix.gc2 + gi);
                         kp = nodes[4 * np + 2];
                         d2 = D[2 * n + c2];
-                        okg = KeyOps<DT>::add(kp, KeyOps<DT>::add(d2, minlast)) <= hik;
+                        okg = KeyOps<DT>::add_lo(kp, KeyOps<DT>::add_lo(d2, minlast)) <= hik;
                         rr = (nodes[4 * np + 3] << 16) | ((uint32_t)rk[2 * n + c2] << 8);
                     }
                     const unsigned mg = __ballot_sync(0xffffffffu, okg);
@@ -632,9 +634,19 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                             const uint32_t j = glist[5 * gp + 0] + (e - glist[5 * gp + 1]);
                             const uint32_t lf = __ldg(ix.leaf + j);
                             const uint32_t c3 = pow2n ? (lf & (uint32_t)(n - 1)) : lf % (uint32_t)n;
-                            const uint32_t key =
-                                KeyOps<DT>::add(glist[5 * gp + 2], KeyOps<DT>::add(glist[5 * gp + 3], D[3 * n + c3]));
-                            if (key > hik || (!first && key < (uint32_t)(lo >> 32))) continue;
+                            const uint32_t kp = glist[5 * gp + 2], d2 = glist[5 * gp + 3], d3 = D[3 * n + c3];
+                            uint32_t key = KeyOps<DT>::add_lo(KeyOps<DT>::add_lo(kp, d2), d3);
+                            if (key > hik) continue;
+                            if (DT == ANN_F32) {
+                                // bounds first; the exact key only for what may lie in the window
+                                if (!first && KeyOps<DT>::add_hi(KeyOps<DT>::add_hi(KeyOps<DT>::up(kp), d2), d3) <
+                                                  (uint32_t)(lo >> 32))
+                                    continue;
+                                const uint32_t rp = glist[5 * gp + 4] >> 16;
+                                key = KeyOps<DT>::sum4(D[sc[rp >> 8]], D[n + sc[n + (rp & 255u)]], d2, d3);
+                                if (key > hik) continue;
+                            }
+                            if (!first && key < (uint32_t)(lo >> 32)) continue;
                             const uint32_t ranks = glist[5 * gp + 4] | rk[3 * n + c3];
                             const uint64_t comp = ((uint64_t)key << 32) | ranks;
                             if (comp <= hi && (first || comp > lo)) {
@@ -679,10 +691,25 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                     } else {
                         c2 = pow2n ? (lf >> logn) : lf / n;
                         c3 = lf - c2 * n;
-                        ksuf = KeyOps<DT>::add(D[2 * n + c2], D[3 * n + c3]);
+                        ksuf = KeyOps<DT>::add_lo(D[2 * n + c2], D[3 * n + c3]);
                     }
-                    const uint32_t key = KeyOps<DT>::add(nodes[4 * nq + 2], ksuf);
-                    if (key > hik || (!first && key < (uint32_t)(lo >> 32))) continue;
+                    const uint32_t kpre = nodes[4 * nq + 2];
+                    uint32_t key = KeyOps<DT>::add_lo(kpre, ksuf);
+                    if (key > hik) continue;
+                    if (DT == ANN_F32) {
+                        // bounds first; the exact key only for what may lie in the window
+                        if (!first && KeyOps<DT>::add_hi(KeyOps<DT>::up(kpre), KeyOps<DT>::up(ksuf)) <
+                                          (uint32_t)(lo >> 32))
+                            continue;
+                        const uint32_t rp = nodes[4 * nq + 3];
+                        const uint32_t d0 = PA == 1 ? D[sc[rp]] : D[sc[rp >> 8]];
+                        const uint32_t d1 = PA == 1 ? D[n + lf] : D[n + sc[n + (rp & 255u)]];
+                        const uint32_t d2 = PA == 1 ? 0u : (nsuf == 1 ? D[2 * n + lf] : D[2 * n + c2]);
+                        const uint32_t d3 = nsuf == 2 ? D[3 * n + c3] : 0u;
+                        key = KeyOps<DT>::sum4(d0, d1, d2, d3);
+                        if (key > hik) continue;
+                    }
+                    if (!first && key < (uint32_t)(lo >> 32)) continue;
                     const uint32_t rsuf = nsuf == 1 ? (uint32_t)rk[(P - 1) * n + lf]
                                                     : (((uint32_t)rk[2 * n + c2] << 8) | rk[3 * n + c3]);
                     const uint32_t ranks = (nodes[4 * nq + 3] << (8 * nsuf)) | rsuf;
@@ -1034,21 +1061,18 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         uint32_t first_keys[kMaxP], last_keys[kMaxP];
         sort_parts<DT>(D, rk, sc, P, n, PA, dp, first_keys, last_keys);
         __syncwarp();
-        // smallest / largest bridge keys and the min-suffix sum, grouped (D0+D1)+(D2+...)
-        auto group_sum = [&](const uint32_t *v) -> uint32_t {
-            uint32_t a = KeyOps<DT>::add(v[0], v[1]);
-            if (P == 2) return a;
-            uint32_t b = v[2];
-            for (int p = 3; p < P; p++) b = KeyOps<DT>::add(b, v[p]);
-            return KeyOps<DT>::add(a, b);
+        // smallest / largest bridge keys (exact sums) and a lower bound of the
+        // smallest suffix sum
+        auto key_sum = [&](const uint32_t *v) -> uint32_t {
+            return KeyOps<DT>::sum4(v[0], v[1], P > 2 ? v[2] : 0u, P > 3 ? v[3] : 0u);
         };
-        kmin = group_sum(first_keys);
-        kmaxall = group_sum(last_keys);
+        kmin = key_sum(first_keys);
+        kmaxall = key_sum(last_keys);
         if (PA == 1) {
             msuf = first_keys[1];
         } else {
             msuf = first_keys[2];
-            for (int p = 3; p < P; p++) msuf = KeyOps<DT>::add(msuf, first_keys[p]);
+            for (int p = 3; p < P; p++) msuf = KeyOps<DT>::add_lo(msuf, first_keys[p]);
         }
         minlast = first_keys[P - 1];
     }
