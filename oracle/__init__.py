@@ -41,7 +41,7 @@ _lock = threading.Lock()
 
 U8, F32 = 0, 1
 STAT_NAMES = ("discovered", "ref_pops", "bridge_pops", "nonempty_bridge_pops", "max_q",
-              "max_frontier", "ms_pushes")
+              "max_frontier", "ms_pushes", "over_limit")
 
 
 def build(force: bool = False) -> str:
@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-ffp-contract=off",
+    subprocess.check_call(["gcc", "-O3", "-std=c11", "-shared", "-fPIC", "-ffp-contract=off",
                            "-o", tmp, _SRC, "-lpthread", "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -74,7 +74,13 @@ def _load():
             lib.oracle_bridge_lists.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, i64, P, P, P, i32]
             lib.oracle_bridge_lists.restype = None
             lib.oracle_search.argtypes = [P, i64, i32, i32, P, i32, i32, i32, P, i64, P, P, P, P,
-                                          i64, P, P, i32, P, P, P, P, i32, i32]
+                                          i64, P, P, i32, P, P, P, P, i32, P, i32]
+            PP = ctypes.POINTER(ctypes.c_void_p)
+            lib.oracle_bridge_graph_near.argtypes = [P, i64, i32, i32, i32, i32, P, i32, i32, P, i32, P,
+                                                     PP, PP, PP, PP, i32]
+            lib.oracle_bridge_graph_near.restype = i64
+            lib.oracle_free.argtypes = [P]
+            lib.oracle_free.restype = None
             lib.oracle_search.restype = i32
             lib.oracle_num_stats.restype = i32
             lib.oracle_pq_encode.argtypes = [P, i64, i32, P, P, i32, i32, P, P]
@@ -210,15 +216,55 @@ def bridge_lists(X: np.ndarray, centers: np.ndarray, t: int, b: int, sel: np.nda
     return counts, refs, keys
 
 
+def bridge_graph_near(X: np.ndarray, centers: np.ndarray, t: int, b: int, queries: np.ndarray, limits,
+                      nthreads: int = 0):
+    """The bridge graph restricted to the bridges whose key to at least one of
+    the queries is <= that query's limit (a bridge a little above may be kept
+    too).  Each kept bridge has its complete list (the b nearest of ALL the
+    references that chose it), as in bridge_graph.  Same dict as
+    bridge_graph; pass `limits` to search(..., bridge_key_limit=) so that a
+    query reaching past its limit is reported instead of searched wrongly."""
+    lib = _load()
+    X = np.ascontiguousarray(X)
+    centers = np.ascontiguousarray(centers)
+    queries = np.ascontiguousarray(queries)
+    assert centers.dtype == X.dtype == queries.dtype
+    P, n, dp = centers.shape
+    N, d = X.shape
+    lim = np.ascontiguousarray(np.broadcast_to(np.asarray(limits, np.float64), (len(queries),)))
+    pb, po, pr, pk = (ctypes.c_void_p() for _ in range(4))
+    M = lib.oracle_bridge_graph_near(_ptr(X), N, d, _dtype_code(X), P, n, _ptr(centers), t, b, _ptr(queries),
+                                     len(queries), _ptr(lim), ctypes.byref(pb), ctypes.byref(po), ctypes.byref(pr),
+                                     ctypes.byref(pk), _threads(nthreads))
+    if M < 0:
+        raise ValueError("oracle_bridge_graph_near: bad arguments")
+    try:
+        offsets = np.ctypeslib.as_array(ctypes.cast(po, ctypes.POINTER(ctypes.c_int64)), (M + 1,)).copy()
+        nnz = int(offsets[M])
+        bridges = (np.ctypeslib.as_array(ctypes.cast(pb, ctypes.POINTER(ctypes.c_uint64)), (M,)).copy()
+                   if M else np.zeros(0, np.uint64))
+        refs = (np.ctypeslib.as_array(ctypes.cast(pr, ctypes.POINTER(ctypes.c_int32)), (nnz,)).copy()
+                if nnz else np.zeros(0, np.int32))
+        keys = (np.ctypeslib.as_array(ctypes.cast(pk, ctypes.POINTER(ctypes.c_double)), (nnz,)).copy()
+                if nnz else np.zeros(0, np.float64))
+    finally:
+        for p_ in (pb, po, pr, pk):
+            lib.oracle_free(p_)
+    return {"bridges": bridges, "offsets": offsets, "refs": refs, "keys": keys, "P": P, "n": n}
+
+
 def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, queries: np.ndarray,
-           k, T, kmax: int | None = None, nthreads: int = 1, trace: bool = False):
+           k, T, kmax: int | None = None, nthreads: int = 1, trace: bool = False, bridge_key_limit=None):
     """Algorithm 1 for each query.  k, T: scalars or per-query arrays.
     graph: (N, R) int32 rows, or an int R to compute each popped row on demand
     (its R nearest other references by linear scan).
 
     Returns (ids (nq, kmax) int32, keys (nq, kmax) float64, stats dict of arrays);
     with trace=True the stats dict also holds 'trace' (nq, max T): the
-    discovered ids in discovery order, -1 after the last."""
+    discovered ids in discovery order, -1 after the last.
+    bridge_key_limit (scalar or per query): bg's lists are complete only for
+    bridges with key <= the limit; a query that would pop a bridge above it
+    stops there and gets stats['over_limit'] = 1."""
     lib = _load()
     X = np.ascontiguousarray(X)
     queries = np.ascontiguousarray(queries)
@@ -245,11 +291,14 @@ def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, quer
     refs = np.ascontiguousarray(bg["refs"], dtype=np.int32)
     cap = int(T.max()) if (trace and nq) else 0
     disc = np.empty((nq, max(cap, 1)), np.int32)
+    lim = None if bridge_key_limit is None else np.ascontiguousarray(
+        np.broadcast_to(np.asarray(bridge_key_limit, np.float64), (nq,)))
     rc = lib.oracle_search(_ptr(X), N, d, _dtype_code(X), None if graph is None else _ptr(graph),
                            R_on_demand if graph is None else graph.shape[1], P, n,
                            _ptr(centers), len(bridges), _ptr(bridges), _ptr(offs), _ptr(refs),
                            _ptr(queries), nq, _ptr(k), _ptr(T), kmax, _ptr(ids), _ptr(keys),
-                           _ptr(st), _ptr(disc) if trace else None, cap, nthreads)
+                           _ptr(st), _ptr(disc) if trace else None, cap, None if lim is None else _ptr(lim),
+                           nthreads)
     if rc != 0:
         raise ValueError("oracle_search: bad arguments")
     out = {name: st[:, i] for i, name in enumerate(STAT_NAMES)}

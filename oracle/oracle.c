@@ -48,10 +48,21 @@ enum { DT_U8 = 0, DT_F32 = 1 };
 /* Distances (Sec. 2: dist(q, x) = ||q - x||_2; Sec. 3.2: squared tables)    */
 /* ------------------------------------------------------------------------ */
 
-/* Squared L2 between a[0..len) and b[0..len) of the given dtype. */
+/* Squared L2 between a[0..len) and b[0..len) of the given dtype.  uint8: the
+   exact integer (each term is at most 255^2, so an int32 sum is exact up to
+   33025 terms).  float32: an fp64 sum of the squared fp64 differences (four
+   interleaved partial sums), rounded once to float32. */
 static double sqdist(const void *a, const void *b, int len, int dtype) {
     if (dtype == DT_U8) {
         const uint8_t *x = (const uint8_t *)a, *y = (const uint8_t *)b;
+        if (len <= 33025) {
+            int32_t s = 0;
+            for (int i = 0; i < len; i++) {
+                int32_t t = (int32_t)x[i] - (int32_t)y[i];
+                s += t * t;
+            }
+            return (double)s;
+        }
         int64_t s = 0;
         for (int i = 0; i < len; i++) {
             int64_t t = (int64_t)x[i] - (int64_t)y[i];
@@ -60,12 +71,21 @@ static double sqdist(const void *a, const void *b, int len, int dtype) {
         return (double)s;
     } else {
         const float *x = (const float *)a, *y = (const float *)b;
-        double s = 0.0;
-        for (int i = 0; i < len; i++) {
-            double t = (double)x[i] - (double)y[i];
-            s += t * t;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int i = 0;
+        for (; i + 4 <= len; i += 4) {
+            double t0 = (double)x[i] - (double)y[i], t1 = (double)x[i + 1] - (double)y[i + 1];
+            double t2 = (double)x[i + 2] - (double)y[i + 2], t3 = (double)x[i + 3] - (double)y[i + 3];
+            s0 += t0 * t0;
+            s1 += t1 * t1;
+            s2 += t2 * t2;
+            s3 += t3 * t3;
         }
-        return (double)(float)s; /* decisions are taken at float32 */
+        for (; i < len; i++) {
+            double t = (double)x[i] - (double)y[i];
+            s0 += t * t;
+        }
+        return (double)(float)((s0 + s1) + (s2 + s3)); /* decisions are taken at float32 */
     }
 }
 
@@ -734,6 +754,174 @@ void oracle_bridge_lists(const void *X, int64_t N, int d, int dtype, int P, int 
     }
 }
 
+/* The bridge graph restricted to the bridges some query can reach below its
+   key limit (Sec. 4.1's definition, restricted): bridge y is kept when
+   key(q, y) <= limit[q] for at least one query q (a bridge slightly above
+   every limit may be kept too: the test only ever admits more), and it keeps
+   the b smallest (key to y, ref id) among ALL references that chose it, so
+   every kept list equals the full bridge graph's list.  Every bridge that is
+   absent has either no reference or keys above every limit.  For indexes
+   whose N*t triples are too many to sort at once.  Each thread keeps a hash
+   map bridge id -> its b best so far; the maps are merged at the end.
+   Outputs are allocated here (release each with oracle_free); returns M. */
+typedef struct {
+    uint64_t id; /* bridge id + 1; 0 = empty slot */
+    int len;
+    double keys[8];
+    int64_t refs[8];
+} near_slot_t;
+
+typedef struct {
+    near_slot_t *slot;
+    int64_t cap, len;
+} near_map_t;
+
+static near_slot_t *near_get(near_map_t *m, uint64_t id) {
+    if (2 * (m->len + 1) > m->cap) {
+        near_slot_t *old = m->slot;
+        int64_t oc = m->cap;
+        m->cap = oc ? 2 * oc : 1024;
+        m->slot = (near_slot_t *)calloc((size_t)m->cap, sizeof(near_slot_t));
+        m->len = 0;
+        for (int64_t i = 0; i < oc; i++)
+            if (old[i].id) {
+                near_slot_t *d = near_get(m, old[i].id - 1);
+                *d = old[i];
+            }
+        free(old);
+    }
+    uint64_t mask = (uint64_t)m->cap - 1, h = mix64(id) & mask;
+    while (m->slot[h].id && m->slot[h].id != id + 1) h = (h + 1) & mask;
+    if (!m->slot[h].id) {
+        m->slot[h].id = id + 1;
+        m->slot[h].len = 0;
+        m->len++;
+    }
+    return &m->slot[h];
+}
+
+typedef struct {
+    const void *X, *centers;
+    int64_t N;
+    int d, dtype, P, n, t, b, nq;
+    const double *qkeys;  /* nq * P * n part keys of the queries, unsorted */
+    const double *limit;  /* nq */
+    near_map_t *maps;     /* one per thread */
+    int64_t next;
+    pthread_mutex_t mu;
+} near_job_t;
+
+typedef struct { near_job_t *job; int th; } near_arg_t;
+
+static void *near_worker(void *arg) {
+    near_arg_t *a = (near_arg_t *)arg;
+    near_job_t *j = a->job;
+    near_map_t *map = &j->maps[a->th];
+    tables_t tb = tables_alloc(j->P, j->n);
+    int32_t cid[MAXP];
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t i = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (i >= j->N) break;
+        tables_build(&tb, row_ptr(j->X, i, j->d, j->dtype), j->d, j->dtype, j->P, j->n, j->centers);
+        mseq_t ms;
+        ms_init(&ms, &tb);
+        ms_item it;
+        for (int s = 0; s < j->t && ms_next(&ms, &it); s++) {
+            for (int p = 0; p < j->P; p++) cid[p] = tb.scid[p * j->n + it.r[p]];
+            int hit = 0;
+            for (int q = 0; q < j->nq && !hit; q++) {
+                /* the query's key to this bridge: exact for bytes; for float32 an
+                   fp64 sum, admitted with a margin above the limit */
+                double k = 0.0;
+                for (int p = 0; p < j->P; p++) k += j->qkeys[((int64_t)q * j->P + p) * j->n + cid[p]];
+                hit = j->dtype == DT_U8 ? k <= j->limit[q] : k <= j->limit[q] * (1.0 + 1e-5);
+            }
+            if (!hit) continue;
+            near_slot_t *e = near_get(map, bridge_id_of(&tb, it.r));
+            topk_insert(e->keys, e->refs, &e->len, j->b, it.key, i);
+        }
+        ms_free(&ms);
+    }
+    tables_free(&tb);
+    return NULL;
+}
+
+static int u64_cmp(const void *a, const void *b) {
+    uint64_t x = *(const uint64_t *)a, y = *(const uint64_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t oracle_bridge_graph_near(const void *X, int64_t N, int d, int dtype, int P, int n, const void *centers,
+                                 int t, int b, const void *queries, int nq, const double *limit,
+                                 uint64_t **out_bridges, int64_t **out_offsets, int32_t **out_refs,
+                                 double **out_keys, int nthreads) {
+    if (b > 8 || P > MAXP) return -1;
+    if (nthreads < 1) nthreads = 1;
+    double *qkeys = (double *)malloc(sizeof(double) * (size_t)nq * P * n);
+    tables_t tb = tables_alloc(P, n);
+    for (int q = 0; q < nq; q++) {
+        tables_build(&tb, row_ptr(queries, q, d, dtype), d, dtype, P, n, centers);
+        memcpy(qkeys + (int64_t)q * P * n, tb.key, sizeof(double) * (size_t)P * n);
+    }
+    tables_free(&tb);
+    near_job_t job = {X, centers, N, d, dtype, P, n, t, b, nq, qkeys, limit, NULL, 0, PTHREAD_MUTEX_INITIALIZER};
+    job.maps = (near_map_t *)calloc((size_t)nthreads, sizeof(near_map_t));
+    near_arg_t *args = (near_arg_t *)malloc(sizeof(near_arg_t) * (size_t)nthreads);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    for (int q = 0; q < nthreads; q++) {
+        args[q].job = &job;
+        args[q].th = q;
+        pthread_create(&th[q], NULL, near_worker, &args[q]);
+    }
+    for (int q = 0; q < nthreads; q++) pthread_join(th[q], NULL);
+    /* merge: every thread's b best of a bridge, the b best overall */
+    near_map_t all = {0};
+    for (int q = 0; q < nthreads; q++) {
+        near_map_t *m = &job.maps[q];
+        for (int64_t i = 0; i < m->cap; i++) {
+            near_slot_t *e = &m->slot[i];
+            if (!e->id) continue;
+            near_slot_t *g = near_get(&all, e->id - 1);
+            for (int r = 0; r < e->len; r++) topk_insert(g->keys, g->refs, &g->len, b, e->keys[r], e->refs[r]);
+        }
+        free(m->slot);
+    }
+    int64_t M = all.len;
+    uint64_t *ids = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(M > 0 ? M : 1));
+    int64_t c = 0;
+    for (int64_t i = 0; i < all.cap; i++)
+        if (all.slot[i].id) ids[c++] = all.slot[i].id - 1;
+    qsort(ids, (size_t)M, sizeof(uint64_t), u64_cmp);
+    int64_t *offs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M + 1));
+    int32_t *refs = (int32_t *)malloc(sizeof(int32_t) * (size_t)(M * b + 1));
+    double *keys = (double *)malloc(sizeof(double) * (size_t)(M * b + 1));
+    int64_t o = 0;
+    for (int64_t i = 0; i < M; i++) {
+        near_slot_t *g = near_get(&all, ids[i]);
+        offs[i] = o;
+        for (int r = 0; r < g->len; r++) {
+            refs[o] = (int32_t)g->refs[r];
+            keys[o] = g->keys[r];
+            o++;
+        }
+    }
+    offs[M] = o;
+    free(all.slot);
+    free(job.maps);
+    free(args);
+    free(th);
+    free(qkeys);
+    *out_bridges = ids;
+    *out_offsets = offs;
+    *out_refs = refs;
+    *out_keys = keys;
+    return M;
+}
+
+void oracle_free(void *p) { free(p); }
+
 /* ------------------------------------------------------------------------ */
 /* Algorithm 1: ANN search over the augmented neighborhood graph (Sec. 4.2)  */
 /* ------------------------------------------------------------------------ */
@@ -786,6 +974,7 @@ enum {
     ST_MAX_Q,          /* largest main-queue length (refs + the bridge) */
     ST_MAX_FRONTIER,   /* largest multi-sequence queue length */
     ST_MS_PUSHES,      /* tuples pushed into the multi-sequence queue */
+    ST_OVER_LIMIT,     /* 1 if a popped bridge's key exceeded the caller's limit (search stopped there) */
     ST_N
 };
 
@@ -821,7 +1010,7 @@ static int64_t bridge_lookup(const index_t *ix, uint64_t id, int64_t *len) {
 /* One query.  ids/keys: kmax outputs; stats: ST_N values. */
 static void search_one(const index_t *ix, const void *q, int k, int T, int kmax, uint8_t *color,
                        int32_t *out_ids, double *out_keys, int64_t *stats, int32_t *disc,
-                       int disc_cap) {
+                       int disc_cap, double bkey_limit) {
     int64_t st[ST_N] = {0};
     /* Mark each reference vector undiscovered. */
     memset(color, 0, (size_t)ix->N);
@@ -870,6 +1059,11 @@ static void search_one(const index_t *ix, const void *q, int k, int T, int kmax,
             alen = ix->R;
         } else {
             st[ST_BRIDGE_POPS]++;
+            if (p.key > bkey_limit) {
+                /* the caller's bridge lists are complete only up to this key */
+                st[ST_OVER_LIMIT] = 1;
+                break;
+            }
             int64_t off = bridge_lookup(ix, bridge_id_of(&tb, cur_ranks), &alen);
             adj = ix->brefs + off;
             if (alen > 0) st[ST_NONEMPTY_POPS]++;
@@ -924,6 +1118,7 @@ typedef struct {
     int64_t *stats;
     int32_t *disc;
     int disc_cap;
+    const double *bkey_limit;
     int64_t next;
     pthread_mutex_t mu;
 } job_t;
@@ -940,7 +1135,8 @@ static void *worker(void *arg) {
         search_one(ix, row_ptr(j->queries, i, ix->d, ix->dtype), j->k[i], j->T[i], j->kmax, color,
                    j->out_ids + i * j->kmax, j->out_keys + i * j->kmax,
                    j->stats ? j->stats + i * ST_N : NULL,
-                   j->disc ? j->disc + i * (int64_t)j->disc_cap : NULL, j->disc_cap);
+                   j->disc ? j->disc + i * (int64_t)j->disc_cap : NULL, j->disc_cap,
+                   j->bkey_limit ? j->bkey_limit[i] : INFINITY);
     }
     free(color);
     return NULL;
@@ -951,15 +1147,19 @@ static void *worker(void *arg) {
    computed on demand by linear scan.
    k[i], T[i]: per-query result count (<= kmax) and budget.
    bridges/boff/brefs: the bridge graph as produced by oracle_bridge_graph.
-   disc (optional, nq*disc_cap): discovered ids in discovery order, -1 after. */
+   disc (optional, nq*disc_cap): discovered ids in discovery order, -1 after.
+   bkey_limit (optional, nq): the bridge lists given are complete only for
+   bridges with key <= bkey_limit[i]; a query that would pop a bridge above
+   it stops there and reports ST_OVER_LIMIT. */
 int oracle_search(const void *X, int64_t N, int d, int dtype, const int32_t *graph, int R, int P,
                   int n, const void *centers, int64_t M, const uint64_t *bridges,
                   const int64_t *boff, const int32_t *brefs, const void *queries, int64_t nq,
                   const int32_t *k, const int32_t *T, int kmax, int32_t *out_ids,
-                  double *out_keys, int64_t *stats, int32_t *disc, int disc_cap, int nthreads) {
+                  double *out_keys, int64_t *stats, int32_t *disc, int disc_cap, const double *bkey_limit,
+                  int nthreads) {
     if (P > MAXP || P < 1 || d % P != 0 || R > 64) return -1;
     index_t ix = {X, N, d, dtype, graph, R, P, n, centers, M, bridges, boff, brefs};
-    job_t job = {&ix, queries, nq, k, T, kmax, out_ids, out_keys, stats, disc, disc_cap, 0,
+    job_t job = {&ix, queries, nq, k, T, kmax, out_ids, out_keys, stats, disc, disc_cap, bkey_limit, 0,
                  PTHREAD_MUTEX_INITIALIZER};
     if (nthreads <= 1) {
         worker(&job);

@@ -541,3 +541,67 @@ def test_bridge_lists_of_selected_bridges_equal_the_bridge_graph(oracle_lib, dty
         assert counts[i] == hi - lo
         np.testing.assert_array_equal(refs[i, :counts[i]], bg["refs"][lo:hi])
         np.testing.assert_array_equal(keys[i, :counts[i]], bg["keys"][lo:hi])
+
+
+# --------------------------------------------------------------------------
+# bridge graph restricted to the bridges queries can reach (Sec. 4.1), and
+# the search's bridge-key limit: the means of checking full-size searches
+# whose whole bridge graph is too large to build
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_restricted_bridge_graph_holds_the_full_lists_of_reachable_bridges(oracle_lib, dtype):
+    rng = np.random.default_rng(21)
+    X, G, C, bg = tiny_index(rng, 400, 16, 2, 12, 8, 30, 3, dtype)
+    Q = gmm(rng, 5, 16, 6, 20.0 if dtype == np.uint8 else 0.15, dtype)
+    P, n, _ = C.shape
+    full = {int(y): list(bg["refs"][bg["offsets"][i]:bg["offsets"][i + 1]]) for i, y in enumerate(bg["bridges"])}
+    # each query's key to every bridge of the full graph (independent statement)
+    qkeys = []
+    for q in Q:
+        D = part_tables(q, C)
+        kq = {}
+        for y in full:
+            cs, v = [], y
+            for _ in range(P):
+                cs.append(v % n)
+                v //= n
+            cs = cs[::-1]
+            kq[y] = bridge_key_py([D[p, cs[p]] for p in range(P)], dtype)
+        qkeys.append(kq)
+    for frac in (0.2, 0.5, 1.0):
+        limits = np.array([np.quantile(list(kq.values()), frac) for kq in qkeys])
+        near = oracle.bridge_graph_near(X, C, 30, 3, Q, limits)
+        got = {int(y): list(near["refs"][near["offsets"][i]:near["offsets"][i + 1]])
+               for i, y in enumerate(near["bridges"])}
+        need = {y for y in full if any(qkeys[i][y] <= limits[i] for i in range(len(Q)))}
+        assert need <= set(got)                                  # every reachable bridge is there
+        for y, lst in got.items():
+            assert lst == full[y]                                # with the full graph's list
+            if y not in need:                                    # extras only within the float margin
+                assert dtype == np.float32 and any(qkeys[i][y] <= limits[i] * (1 + 1e-5) for i in range(len(Q)))
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.float32])
+def test_search_with_restricted_bridges_equals_full_search_or_reports(oracle_lib, dtype):
+    rng = np.random.default_rng(22)
+    X, G, C, bg = tiny_index(rng, 800, 16, 2, 24, 6, 10, 3, dtype, ncomp=12)
+    Q = gmm(rng, 12, 16, 12, 20.0 if dtype == np.uint8 else 0.15, dtype)
+    want_i, want_k, want_s = oracle.search(X, G, C, bg, Q, 10, 60)
+    assert not want_s["over_limit"].any()
+    kth = oracle.exact_knn(X, Q, 20)[1][:, -1]
+    partial = 0
+    for scale in (0.5, 1.0, 1.2, 1.5, 2.0):
+        limits = kth * scale
+        near = oracle.bridge_graph_near(X, C, 10, 3, Q, limits)
+        got_i, got_k, got_s = oracle.search(X, G, C, near, Q, 10, 60, bridge_key_limit=limits)
+        ok = got_s["over_limit"] == 0
+        np.testing.assert_array_equal(got_i[ok], want_i[ok])
+        np.testing.assert_array_equal(got_k[ok], want_k[ok])
+        if scale == 0.5:
+            assert not ok.any()       # a tight limit is reported, not searched past
+        partial += ok.any() and len(near["bridges"]) < len(bg["bridges"])
+    assert partial >= 2               # complete searches on graphs missing some bridges
+    # an unbounded limit over the full graph changes nothing
+    i2, k2, s2 = oracle.search(X, G, C, bg, Q, 10, 60, bridge_key_limit=np.inf)
+    np.testing.assert_array_equal(i2, want_i)
