@@ -3,12 +3,18 @@
 search (Algorithm 1 of arXiv:1312.3062) on one GB300, persistent vs plain vs
 served forms, with p50/p99 latency of the served form.
 
-Workload: SIFT-shaped, N = 1,000,000 x 128 uint8 references (seeded
-1,000-component Gaussian mixture), 10,000 queries from the same mixture; exact
-kNN graph R = 20 (GPU), P = 4 x n = 256 part dictionaries (GPU k-means, 10
-iterations on all rows), bridge graph t = 100, b <= 5 (GPU).  T90 = the
-smallest budget on the grid {64, 90, 128, 181, 256, ...} with mean
-recall@10 >= 0.9; every timed step searches all 10,000 queries at T90, k = 10.
+Headline workload (default): the served SIFT-shaped index, N = 10,000,000 x
+128 uint8 references (seeded 1,000-component Gaussian mixture), resident in
+HBM; 10,000 queries from the same mixture; exact kNN graph R = 16 (GPU,
+tensor cores), P = 4 x n = 256 part dictionaries (GPU k-means, 10
+iterations on a seeded 1M-row sample), bridge graph t = 100, b <= 5 (GPU).
+T90 = the smallest budget on the grid {64, 90, 128, 181, 256, ...} (steps of
+sqrt 2) with mean recall@10 >= 0.9; every timed step searches all 10,000
+queries at T90, k = 10.  The served form replays Poisson arrivals of 1-512
+query requests at T90 and, separately, the workload's own request mix (k in
+{1, 10, 100}, T in {128, 512, 2048}) against the plain form on that mix.
+The SIFT-shaped 1M index (R = 20) is measured the same way as an extra
+entry.  --workload 2 makes sift1m the headline instead.
 
 One step = one pass of the whole hot path over the 10,000-query batch with
 inputs resident in HBM.  L2 is flushed (256 MB write) before every timed step.
@@ -39,7 +45,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = 2
+WORKLOAD = 5
 T_GRID = [64, 90, 128, 181, 256, 362, 512, 724, 1024, 1448, 2048, 2896, 4096, 5792, 8192]
 K = 10
 METRIC = "queries/s at recall@10=0.9, persistent/served vs plain GPU search; p50/p99 ms"
@@ -64,9 +70,10 @@ def parse():
     ap.add_argument("--knn-approx", action="store_true",
                     help="workload 2 or 5: approximate kNN graph versus the exact one (build time, graph "
                          "recall; on workload 2 also the search each graph gives)")
-    ap.add_argument("--workload", type=int, default=2, choices=[2, 3, 4, 5],
-                    help="2 sift1m (default, the headline); 3 gist1m uneven k/T; 4 hog4m recall-vs-T; "
-                         "5 sift10m served")
+    ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 4, 5],
+                    help="5 sift10m served (default, the headline); 2 sift1m; 3 gist1m uneven k/T; "
+                         "4 hog4m recall-vs-T")
+    ap.add_argument("--no-extra", action="store_true", help="skip the sift1m entry of the sift10m headline")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = args.workload
@@ -159,13 +166,14 @@ class ClockSampler:
 # workload
 # --------------------------------------------------------------------------
 
-def build_workload(args, torch, ann, datagen, log):
-    spec = dict(datagen.WORKLOADS[WORKLOAD])
-    N = args.N or spec["N"]
-    nq = args.nq or spec["nq"]
+def build_workload(args, torch, ann, datagen, log, workload=None, full=False):
+    workload = WORKLOAD if workload is None else workload
+    spec = dict(datagen.WORKLOADS[workload])
+    N = spec["N"] if full else (args.N or spec["N"])
+    nq = spec["nq"] if full else (args.nq or spec["nq"])
     t0 = time.time()
-    Xh = datagen.references(WORKLOAD, N)
-    Qh = datagen.queries(WORKLOAD, nq)
+    Xh = datagen.references(workload, N)
+    Qh = datagen.queries(workload, nq)
     log(f"data {N}x{spec['d']} + {nq} queries in {time.time() - t0:.1f}s")
     X = torch.from_numpy(Xh).cuda()
     Q = torch.from_numpy(Qh).cuda()
@@ -174,10 +182,10 @@ def build_workload(args, torch, ann, datagen, log):
     torch.cuda.synchronize()
     t_knn = time.time() - t0
     t0 = time.time()
-    train_rows = datagen.training_rows(WORKLOAD, N)
+    train_rows = datagen.training_rows(workload, N)
     train = X if train_rows is None else X[torch.from_numpy(train_rows).cuda()]
     C = ann.ann_train_centers(train.contiguous(), spec["P"], spec["n"], 10,
-                              datagen.kmeans_init_rows(WORKLOAD, train.shape[0], spec["n"]))
+                              datagen.kmeans_init_rows(workload, train.shape[0], spec["n"]))
     t_km = time.time() - t0
     t0 = time.time()
     index = ann.Index.create(X, G, C, t=spec["t"], b=spec["b"])
@@ -188,7 +196,8 @@ def build_workload(args, torch, ann, datagen, log):
     gt_ids, gt_keys = ann.ann_exact_knn(X, Q, K)
     torch.cuda.synchronize()
     log(f"ground truth {time.time() - t0:.1f}s; index M={info['M']} alpha={info['alpha']:.3g}")
-    return dict(spec=spec, N=N, nq=nq, X=X, Q=Q, Xh=Xh, Qh=Qh, index=index, gt_ids=gt_ids, gt_keys=gt_keys,
+    return dict(workload=workload, spec=spec, N=N, nq=nq, X=X, Q=Q, Xh=Xh, Qh=Qh, index=index, gt_ids=gt_ids,
+                gt_keys=gt_keys,
                 info=info, G=G, C=C, build_s={"knn_graph": t_knn, "kmeans": t_km, "bridge_graph": t_bg})
 
 
@@ -282,7 +291,7 @@ def served_run(torch, ann, W, T, datagen, log, duration_s=2.0, load_fracs=(0.25,
     out = []
     for frac in load_fracs:
         rate = frac * plain_qps
-        arrivals, sizes = datagen.poisson_requests(WORKLOAD, 400000, rate_qps=rate)
+        arrivals, sizes = datagen.poisson_requests(W["workload"], 400000, rate_qps=rate)
         n = int(np.searchsorted(arrivals, duration_s))
         arrivals = np.ascontiguousarray(arrivals[:n], np.float64)
         sizes = np.ascontiguousarray(sizes[:n], np.int32)
@@ -397,12 +406,42 @@ def main():
     if args.build_only:
         torch.cuda.synchronize()
         return
-    if WORKLOAD != 2:
+    if WORKLOAD in (3, 4):
         return run_other(args, rank, ws, log, torch, ann, datagen, W)
     if args.ablation:
         return run_ablation(args, rank, ws, log, torch, ann, datagen, W)
+    head = measure(args, rank, ws, log, torch, ann, datagen, W, headline=True)
+    extra = None
+    if WORKLOAD == 5 and not args.no_extra:
+        # the SIFT-shaped 1M index, measured the same way (not the headline)
+        W["index"].free()
+        del W
+        torch.cuda.empty_cache()
+        W2 = build_workload(args, torch, ann, datagen, log, workload=2, full=True)
+        extra = measure(args, rank, ws, log, torch, ann, datagen, W2, headline=False)
+        extra = {k: extra[k] for k in ("config", "value", "ms_per_step", "plain", "persistent", "uneven", "roofline",
+                                       "search_stats_mean_per_query", "e2e")}
+    if rank == 0:
+        line = head["line"]
+        if extra is not None:
+            line["sift1m"] = extra
+        print(json.dumps(line), flush=True)
+    barrier(ws)
+
+
+WORKLOAD_NAMES = {
+    2: "sift1m: N=%d x 128 uint8, %d queries, kNN graph R=20, P=4 x n=256, b<=5, t=100",
+    5: "sift10m (served SIFT-shaped): N=%d x 128 uint8 resident in HBM, %d queries, kNN graph R=16, "
+       "P=4 x n=256, b<=5, t=100",
+}
+
+
+def measure(args, rank, ws, log, torch, ann, datagen, W, headline):
+    """T90 sweep, then plain / persistent / uneven / e2e / served timings at
+    T90 with k = 10, the roofline of the search kernel and (headline only)
+    the served request mix of the workload and the CPU oracle baseline."""
     T90, rec, table = sweep_t90(args, torch, ann, W, log)
-    log(f"T90={T90} recall@10={rec:.4f}")
+    log(f"{W['spec']['name']}: T90={T90} recall@10={rec:.4f}")
     nq = W["nq"]
     index, Q = W["index"], W["Q"]
     stream = torch.cuda.Stream()
@@ -422,7 +461,7 @@ def main():
     # persistent form (CUDA graph replay), the headline
     barrier(ws)
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
+    clk = ClockSampler(torch.cuda.current_device())
     clk.start()
     t_pers = time_steps(torch, lambda: step(1), args.steps, args.warmup, flush, stream)
     torch.cuda.synchronize()
@@ -451,16 +490,16 @@ def main():
     traffic = None
     prof = os.path.join(ROOT, "profiles", "search_kernel_traffic.json")
     if os.path.exists(prof):
-        import hashlib
         pj = json.load(open(prof))
         digest = search_kernel_digest()
-        if (pj.get("T") == T90 and pj.get("nq") == nq and pj.get("N") == W["N"]
-                and pj.get("kernel_source_sha256") == digest):
-            traffic = pj.get("dram_bytes_per_launch")
+        for e in (pj if isinstance(pj, list) else [pj]):
+            if (e.get("T") == T90 and e.get("nq") == nq and e.get("N") == W["N"]
+                    and e.get("kernel_source_sha256") == digest):
+                traffic = e.get("dram_bytes_per_launch")
 
     # uneven batch: per-query budgets T90/4, T90/2, T90 (plain sizes for the largest; persistent buckets)
     mix_choices = sorted({max(32, T90 // 4), max(32, T90 // 2), T90})
-    T_mix = torch.from_numpy(datagen.uneven_budgets(WORKLOAD, nq, mix_choices)).cuda()
+    T_mix = torch.from_numpy(datagen.uneven_budgets(W["workload"], nq, mix_choices)).cuda()
 
     def step_mix(mode):
         ann.ann_search_batch(index, Q, K, T_mix, kmax=K, mode=mode, out_ids=out_ids, out_keys=out_keys,
@@ -493,12 +532,14 @@ def main():
     e2e_ms = max_over_ranks(sum(t_e2e), ws, "cuda")
     e2e_value = nq * ws * args.steps / (e2e_ms / 1e3)
 
-    served = None
-    if not args.no_serve and rank == 0:
+    served = served_mix = None
+    if headline and not args.no_serve and rank == 0:
         served = served_run(torch, ann, W, T90, datagen, log, plain_qps=plain_qps)
+        if W["workload"] == 5:
+            served_mix = served_request_mix(args, torch, ann, W, datagen, log, stream, flush)
 
     cpu_baseline = None
-    if not args.no_cpu_baseline and rank == 0 and ws == 1:
+    if headline and not args.no_cpu_baseline and rank == 0 and ws == 1:
         index_host_copies(torch, ann, W)
         qps, cores, n2, passes, el = oracle_sample_qps(torch, ann, W, T90)
         cpu_baseline = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
@@ -506,46 +547,74 @@ def main():
                                   f"one query per thread, {el:.1f}s; search only, on the index arrays the GPU "
                                   f"built"}
 
-    if rank == 0:
-        line = {
-            "metric": METRIC,
-            "value": value,
-            "unit": "queries/s",
-            "n_gpus": ws,
-            "steps": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": ms_per_step,
-            "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "u8",
-            "data": "synthetic (seeded SIFT-shaped Gaussian mixture; the paper's datasets are not available)",
-            "config": {"workload": f"sift1m: N={W['N']} x 128 uint8, {nq} queries, kNN graph R=20, "
-                                   f"P=4 x n=256, b<=5, t=100",
-                       "T": T90, "k": K, "recall@10": rec, "mode": "persistent (CUDA graph, budget buckets)",
-                       "l2": "flushed before every timed step (256 MB write)",
-                       "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "recall_vs_T": table},
-            "plain": {"qps": plain_qps, "ms_per_step": statistics.mean(t_plain)},
-            "persistent": {"qps": value / ws, "ms_per_step": ms_per_step},
-            "served": served,
-            "uneven": uneven,
-            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.numel()),
-                    "d2h_bytes_per_step": int(nq * K * 8)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "search_kernel<u8> (plain launch)",
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
-            "search_stats_mean_per_query": search_stats,
-            "cpu_baseline": cpu_baseline,
-            "clocks": clocks,
-            "gpu_launches": args.steps,  # uniform budget: one search kernel per replayed graph
-            "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
-                                                   "bytes_bridges")}, "build_s": W["build_s"]},
-        }
-        print(json.dumps(line), flush=True)
-    barrier(ws)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic (seeded SIFT-shaped Gaussian mixture; the paper's datasets are not available)",
+        "config": {"workload": WORKLOAD_NAMES[W["workload"]] % (W["N"], nq),
+                   "T": T90, "k": K, "recall@10": rec, "mode": "persistent (CUDA graph, budget buckets)",
+                   "l2": "flushed before every timed step (256 MB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "recall_vs_T": table},
+        "plain": {"qps": plain_qps, "ms_per_step": statistics.mean(t_plain)},
+        "persistent": {"qps": value / ws, "ms_per_step": ms_per_step},
+        "served": served,
+        "served_request_mix": served_mix,
+        "uneven": uneven,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(Q.numel()),
+                "d2h_bytes_per_step": int(nq * K * 8)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "search_kernel<u8> (plain launch)",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "search_stats_mean_per_query": search_stats,
+        "cpu_baseline": cpu_baseline,
+        "clocks": clocks,
+        "gpu_launches": args.steps,  # uniform budget: one search kernel per replayed graph
+        "index": {**{k: W["info"][k] for k in ("M", "bridged_refs", "alpha", "bytes_vectors", "bytes_graph",
+                                               "bytes_bridges")}, "build_s": W["build_s"]},
+    }
+    return {"line": line, "config": line["config"], "value": value, "ms_per_step": ms_per_step,
+            "plain": line["plain"], "persistent": line["persistent"], "uneven": uneven, "roofline": line["roofline"],
+            "search_stats_mean_per_query": search_stats, "e2e": line["e2e"]}
+
+
+def served_request_mix(args, torch, ann, W, datagen, log, stream, flush):
+    """The served workload's own request mix (per query k in {1, 10, 100} and
+    T in {128, 512, 2048}): plain and persistent forms over the whole mixed
+    batch, then the served form at fractions of the plain capacity."""
+    nq = W["nq"]
+    kq, Tq = datagen.per_query_params(W["workload"], nq)
+    kmax = int(kq.max())
+    kd, Td = torch.from_numpy(kq).cuda(), torch.from_numpy(Tq).cuda()
+    ids = torch.empty((nq, kmax), dtype=torch.int32, device="cuda")
+    keys = torch.empty((nq, kmax), dtype=torch.int32, device="cuda")
+    stt = torch.empty((nq,), dtype=torch.int32, device="cuda")
+
+    def step(mode):
+        ann.ann_search_batch(W["index"], W["Q"], kd, Td, kmax=kmax, mode=mode, out_ids=ids, out_keys=keys,
+                             out_status=stt, stream=stream)
+
+    t_plain = time_steps(torch, lambda: step(0), args.steps, args.warmup, flush, stream)
+    t_pers = time_steps(torch, lambda: step(1), args.steps, args.warmup, flush, stream)
+    rec = recall_at_10(torch, ids, W, kd)
+    plain_qps = nq * args.steps / (sum(t_plain) / 1e3)
+    out = {"k_choices": [1, 10, 100], "T_choices": [128, 512, 2048], "recall": rec, "plain_qps": plain_qps,
+           "persistent_qps": nq * args.steps / (sum(t_pers) / 1e3)}
+    log(f"request mix: recall {rec:.4f}, plain {plain_qps:.0f} q/s, persistent {out['persistent_qps']:.0f} q/s")
+    out["served"] = served_run(torch, ann, W, 0, datagen, log, plain_qps=plain_qps, kq=kq, Tq=Tq,
+                               load_fracs=(0.25, 0.5, 0.75, 1.0))
+    return out
 
 
 def run_other(args, rank, ws, log, torch, ann, datagen, W):
@@ -767,6 +836,8 @@ def reference_arm(args, rank, ws, log):
     oracle.build()
     from paper_1312_3062_gb300 import ann, datagen
     torch.cuda.set_device(0)
+    if WORKLOAD not in WORKLOAD_NAMES:
+        raise SystemExit("--impl reference times the headline workloads (2 or 5)")
     W = build_workload(args, torch, ann, datagen, log)
     T90, rec, _ = sweep_t90(args, torch, ann, W, log)
     index_host_copies(torch, ann, W)
@@ -787,8 +858,8 @@ def reference_arm(args, rank, ws, log):
             "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"sift1m: N={W['N']} x 128 uint8, {W['nq']} queries, kNN graph R=20, "
-                                   f"P=4 x n=256, b<=5, t=100", "T": T90, "k": K, "recall@10": rec},
+            "config": {"workload": WORKLOAD_NAMES[W["workload"]] % (W["N"], W["nq"]), "T": T90, "k": K,
+                       "recall@10": rec},
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} step(s) of all {W['nq']} queries, one query per thread, "
                                        f"{el:.1f}s; search only, on the index arrays the GPU built"},

@@ -144,6 +144,23 @@ def test_gist1m_sampled_uneven_search(gist1m):
     assert np.all(np.isinf(got[~fin]))
 
 
+def test_gist1m_sampled_large_budget_search(gist1m):
+    # queries of the same batch with budgets in the storm regime (T >= 4096,
+    # where the component is exhausted and hundreds of bridges are popped)
+    # and in between (1024 <= T < 4096)
+    ann, X, Q, C, G, ix, k, T, ids, keys, st = gist1m
+    bg = gist1m_bg[0] if gist1m_bg[0] is not None else oracle.bridge_graph(X, C, 100, 5)
+    rng = np.random.default_rng(34)
+    sel = np.sort(np.concatenate([rng.choice(np.flatnonzero(T >= 4096), 6, replace=False),
+                                  rng.choice(np.flatnonzero((T >= 1024) & (T < 4096)), 2, replace=False)]))
+    wi, wk, wst = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=len(sel))
+    assert (wst["bridge_pops"] > 100).sum() >= 4     # the storm regime is exercised
+    np.testing.assert_array_equal(ids[sel], wi)
+    fin = np.isfinite(wk)
+    got = keys[sel].view(np.float32).astype(np.float64)
+    np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)
+
+
 # ---------------------------------------------------------------------------
 # The largest indexes: SIFT-shaped 10M uint8 (R = 16) and HOG-shaped 4M
 # float32 (R = 16, 330M non-empty bridges).  Their full bridge graphs are too
@@ -197,18 +214,131 @@ def _check_big(ann, X, C, G, ix, R, seed):
     assert counts.max() > 0 and counts.min() == 0   # both present and absent ids were checked
 
 
-def test_sift10m_sampled_knn_rows_and_bridge_lists():
+def oracle_search_big(X, R, C, Q, k, T, kmax, limits):
+    """Algorithm 1 for sampled queries of an index whose whole bridge graph is
+    too large for the oracle: bridge lists restricted to the bridges each
+    query can reach below a key limit (complete lists, computed from every
+    reference), kNN rows computed on demand by linear scan.  A query that
+    would pop a bridge above its limit is reported by the oracle and run
+    again with the limit doubled."""
+    nq = len(Q)
+    k = np.broadcast_to(np.asarray(k, np.int32), (nq,))
+    T = np.broadcast_to(np.asarray(T, np.int32), (nq,))
+    limits = np.asarray(limits, np.float64).copy()
+    ids = np.full((nq, kmax), -1, np.int32)
+    keys = np.full((nq, kmax), np.inf)
+    done = np.zeros(nq, bool)
+    for _ in range(10):
+        todo = np.flatnonzero(~done)
+        bg = oracle.bridge_graph_near(X, C, 100, 5, Q[todo], limits[todo])
+        wi, wk, st = oracle.search(X, R, C, bg, Q[todo], k[todo], T[todo], kmax=kmax, nthreads=len(todo),
+                                   bridge_key_limit=limits[todo])
+        ok = st["over_limit"] == 0
+        ids[todo[ok]], keys[todo[ok]] = wi[ok], wk[ok]
+        done[todo[ok]] = True
+        if done.all():
+            return ids, keys
+        limits[todo[~ok]] *= 2
+    raise AssertionError("bridge key limits did not converge")
+
+
+def first_limits(X, Q, T):
+    """Starting key limits: the key of each query's min(T, 256)-th nearest
+    reference (the doubling in oracle_search_big takes care of the rest)."""
+    kk = int(min(256, np.max(T)))
+    _, kd = oracle.exact_knn(X, Q, kk)
+    col = np.minimum(np.broadcast_to(np.asarray(T), (len(Q),)), kk) - 1
+    return kd[np.arange(len(Q)), col]
+
+
+@pytest.fixture(scope="module")
+def sift10m():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     ann, X, C, G, ix = _big_index(5, 16, 5055)
-    _check_big(ann, X, C, G, ix, 16, 55)
+    yield ann, X, C, G, ix
     ix.free()
 
 
-def test_hog4m_sampled_knn_rows_and_bridge_lists():
+@pytest.fixture(scope="module")
+def hog4m():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     ann, X, C, G, ix = _big_index(4, 16, 4044)
+    yield ann, X, C, G, ix
+    ix.free()
+
+
+def test_sift10m_sampled_knn_rows_and_bridge_lists(sift10m):
+    ann, X, C, G, ix = sift10m
+    _check_big(ann, X, C, G, ix, 16, 55)
+
+
+def test_sift10m_served_mix_search(sift10m):
+    # the served workload's request mix (per query k in {1, 10, 100}, T in
+    # {128, 512, 2048}) over all 10,000 queries in the persistent form, and
+    # the same queries through the server; 16 sampled queries against the
+    # oracle, bit-exact
+    ann, X, C, G, ix = sift10m
+    Q = datagen.queries(5)
+    k, T = datagen.per_query_params(5, len(Q))
+    ids, keys, st = ann.ann_search_batch(ix, torch.from_numpy(Q).cuda(), torch.from_numpy(k).cuda(),
+                                         torch.from_numpy(T).cuda(), kmax=100, mode=1)
+    torch.cuda.synchronize()
+    assert np.all(st.cpu().numpy() == 0)
+    ids, keys = ids.cpu().numpy(), ann.keys_as_uint32(keys)
+    rng = np.random.default_rng(505)
+    sel = np.sort(np.concatenate([rng.choice(np.flatnonzero(T == t), c, replace=False)
+                                  for t, c in ((128, 5), (512, 5), (2048, 6))]))
+    wi, wk = oracle_search_big(X, 16, C, Q[sel], k[sel], T[sel], 100, first_limits(X, Q[sel], T[sel]))
+    np.testing.assert_array_equal(ids[sel], wi)
+    np.testing.assert_array_equal(keys[sel].astype(np.float64), wk)
+    # the same sampled queries submitted to the server, one request each
+    import ctypes
+    import time
+    srv = ctypes.c_void_p()
+    ann.check(ann.lib.ann_server_create(ix.handle, 64 << 20, 3, ctypes.byref(srv)))
+    try:
+        tickets = []
+        for i in sel:
+            q, kk, TT = (np.ascontiguousarray(a[i:i + 1]) for a in (Q, k, T))
+            tk = ctypes.c_uint64()
+            ann.check(ann.lib.ann_serve_submit(srv, q.ctypes.data, 1, kk.ctypes.data, TT.ctypes.data,
+                                               ctypes.byref(tk)))
+            tickets.append(tk.value)
+        deadline = time.time() + 120
+        for j, tk in enumerate(tickets):
+            kj = int(k[sel[j]])
+            si, sk, ss = np.empty((1, kj), np.int32), np.empty((1, kj), np.int32), np.empty(1, np.int32)
+            while ann.lib.ann_serve_poll(srv, tk, si.ctypes.data, sk.ctypes.data, ss.ctypes.data) != ann.ANN_OK:
+                assert time.time() < deadline, "server did not finish"
+                time.sleep(0.001)
+            assert ss[0] == 0
+            np.testing.assert_array_equal(si[0], wi[j, :kj])
+            np.testing.assert_array_equal(sk[0].view(np.uint32).astype(np.float64), wk[j, :kj])
+    finally:
+        ann.lib.ann_server_destroy(srv)
+
+
+def test_hog4m_sampled_knn_rows_and_bridge_lists(hog4m):
+    ann, X, C, G, ix = hog4m
     assert ix.info()["groups"] > 0   # dense bridge graph: the c2 group level is built
     _check_big(ann, X, C, G, ix, 16, 44)
-    ix.free()
+
+
+def test_hog4m_sampled_search(hog4m):
+    # 20,000 queries at T in {256, 1024, 4096}, k = 10; 16 sampled queries
+    # against the oracle: identical ids, keys within 1e-5 relative
+    ann, X, C, G, ix = hog4m
+    Q = datagen.queries(4)
+    rng = np.random.default_rng(404)
+    for T, c in ((256, 8), (1024, 6), (4096, 2)):
+        ids, keys, st = ann.ann_search_batch(ix, torch.from_numpy(Q).cuda(), 10, T, kmax=10, mode=1)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        sel = np.sort(rng.choice(len(Q), c, replace=False))
+        wi, wk = oracle_search_big(X, 16, C, Q[sel], 10, T, 10, first_limits(X, Q[sel], T))
+        np.testing.assert_array_equal(ids.cpu().numpy()[sel], wi)
+        got = keys.cpu().numpy()[sel].astype(np.float64)
+        fin = np.isfinite(wk)
+        np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)
