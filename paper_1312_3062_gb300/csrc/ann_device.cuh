@@ -246,6 +246,12 @@ __device__ __forceinline__ uint32_t f32_exact_sum(uint32_t a, uint32_t b, uint32
     return ((uint32_t)E << 23) | ((uint32_t)q & 0x7fffffu);
 }
 
+// out of line: the walks call it only for leaves that may lie in the window,
+// and keeping its registers out of the search loop avoids spills there
+static __device__ __noinline__ uint32_t f32_exact_sum_call(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    return f32_exact_sum(a, b, c, d);
+}
+
 __device__ __forceinline__ uint32_t f32_next_up(uint32_t x) { return x == 0x7f800000u ? x : x + 1; }
 
 template <int DT> struct KeyOps;
@@ -275,7 +281,7 @@ template <> struct KeyOps<ANN_F32> {
         return __float_as_uint(__fadd_ru(__uint_as_float(a), __uint_as_float(b)));
     }
     static __device__ __forceinline__ uint32_t sum4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-        return f32_exact_sum(a, b, c, d);
+        return f32_exact_sum_call(a, b, c, d);
     }
 };
 

@@ -37,8 +37,10 @@ static int device_props() {
     return ANN_OK;
 }
 
-// Budgets from this size on use sorted bridge windows in global scratch: one
-// walk then serves many batches, which pays off when queries pop many bridges.
+// Budgets from this size on use per-warp global scratch: sorted bridge windows
+// (one walk then serves many batches, which pays off when queries pop many
+// bridges), and the queue's overflow and the visited set, so the shared-memory
+// slice of a query no longer grows with its budget.
 static const int kWindowedFromT = 1024;
 
 // Launch configuration for a budget bucket: warps per CTA and batch capacity.
@@ -57,7 +59,7 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     t.bcap = capT >= kWindowedFromT ? 128 : 64;
     t.stage = true;
     WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b, ix.R, true,
-                               ix.ngroups > 0);
+                               ix.ngroups > 0, capT >= kWindowedFromT);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
     // register-file limit of the kernel (both instantiations use the same budget)
@@ -120,7 +122,7 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     const Tune tn = tune ? *tune : choose_tune(A.ix, capT, A.kmax);
     A.bcap = tn.bcap;
     A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b, A.ix.R,
-                      tn.stage, A.ix.ngroups > 0);
+                      tn.stage, A.ix.ngroups > 0, capT >= kWindowedFromT);
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
@@ -129,6 +131,11 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     uint32_t gcap = (uint32_t)(2 * capT);
     if (gcap > 8192) gcap = 8192;
     A.gcap = win ? gcap : 0;
+    // per-warp scratch: windows, then the queue's overflow, then the visited set
+    auto al = [](uint64_t x) { return (x + 255) & ~(uint64_t)255; };
+    A.spill_off = win ? al((uint64_t)gcap * 24) : 0;
+    A.hash_off = win ? A.spill_off + al(8ull * (uint64_t)capT) : 0;
+    A.wstride = win ? A.hash_off + al(4ull << A.L.hash_log) : 0;
     size_t smem = (size_t)A.L.total * tn.warps;
     if (smem > g_smem_optin) return fail(ANN_ERR_CAPACITY, "per-query state exceeds shared memory");
     int blocks_per_sm = 0;
@@ -158,7 +165,7 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     cfg.block = dim3(threads);
     cfg.smem = smem;
     cfg.win = win;
-    cfg.scratch_bytes = win ? (size_t)want * tn.warps * gcap * 24 : 0;
+    cfg.scratch_bytes = win ? (size_t)want * tn.warps * A.wstride : 0;
     return ANN_OK;
 }
 

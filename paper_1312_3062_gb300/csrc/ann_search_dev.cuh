@@ -52,11 +52,17 @@ struct WarpLayout {
 // adjacency list of vectors fits in this many bytes.
 constexpr uint32_t kStageBytes = 4096;
 
+// Large-budget ("spilling") kernels keep at most this many queue entries in
+// shared memory; the rest of the queue and the visited set live in the
+// warp's global scratch, so a query's shared-memory slice does not grow with
+// the budget.
+constexpr uint32_t kSpillHeap = 512;
+
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
                                                   int kmax, int bcap, int b, int R, bool stage = true,
-                                                  bool grouped = false) {
+                                                  bool grouped = false, bool spill = false) {
     WarpLayout L;
     uint32_t o = 0;
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
@@ -66,13 +72,14 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.sc = o;     o = align_up(o + (uint32_t)PA * n, 16);
     uint32_t lpn = 1;
     while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
-    uint32_t hc = (uint32_t)capT > lpn ? (uint32_t)capT : lpn;
+    const uint32_t qcap = spill && (uint32_t)capT > kSpillHeap ? kSpillHeap : (uint32_t)capT;
+    uint32_t hc = qcap > lpn ? qcap : lpn;
     L.heap_cap = hc;
     L.heap = o;   o = align_up(o + 8u * hc, 16);
     uint32_t hl = 5;
     while ((1u << hl) < 2u * (uint32_t)capT) hl++;
     L.hash_log = hl;
-    L.hash = o;   o = align_up(o + 4u * (1u << hl), 16);
+    L.hash = o;   o = align_up(o + (spill ? 0u : 4u * (1u << hl)), 16);  // spilling: in global scratch
     L.rbuf = o;   o = align_up(o + 8u * kmax, 16);
     L.bcap = (uint32_t)bcap;
     L.bkey = o;   o = align_up(o + 8u * bcap, 16);
@@ -131,10 +138,13 @@ struct SearchArgs {
     int capT;
     int bcap;
     WarpLayout L;
-    // per-warp global scratch for sorted bridge windows (large-budget kernels):
-    // gcap x (2 keys + 2 values)
+    // per-warp global scratch of the large-budget kernels, wstride bytes per
+    // warp: sorted bridge windows (gcap x (2 keys + 2 values)) at 0, the
+    // queue's overflow (capT entries) at spill_off, the visited set
+    // (2^hash_log slots) at hash_off
     uint8_t *gscratch;
     uint32_t gcap;
+    uint64_t wstride, spill_off, hash_off;
 };
 
 // ---------------------------------------------------------------------------
@@ -175,6 +185,43 @@ __device__ __forceinline__ void hash_add(uint32_t *H, uint32_t log, uint32_t x) 
         if (prev == 0 || prev == x + 1) return;
         h = (h + 1) & mask;
     }
+}
+
+// The same open-addressing table in global memory (large-budget kernels):
+// one probe step reads the aligned 32-byte sector of eight slots holding the
+// current slot, so an insertion or a lookup usually costs one memory round
+// trip.  Only the owning warp reads and writes its table; plain loads and
+// stores ordered by __syncwarp keep it coherent.  Returns as hash_find.
+__device__ __forceinline__ bool ghash_find(const uint32_t *G, uint32_t log, uint32_t x, uint32_t &slot) {
+    const uint32_t mask = (1u << log) - 1;
+    uint32_t h = hslot(x, log), seen = 0;
+    while (seen <= mask) {
+        const uint32_t base = h & ~7u;
+        const uint4 *p = (const uint4 *)(G + base);
+        const uint4 a = __ldcg(p), b = __ldcg(p + 1);  // at L2: insertions by CAS bypass L1
+        const uint32_t v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t eq = 0, em = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            eq |= (uint32_t)(v[j] == x + 1) << j;
+            em |= (uint32_t)(v[j] == 0) << j;
+        }
+        const uint32_t from = h & 7u;
+        const uint32_t hit = ((eq | em) >> from) << from;
+        if (hit) {
+            const uint32_t j = __ffs(hit) - 1;
+            slot = base + j;
+            return (eq >> j) & 1u;
+        }
+        seen += 8 - from;
+        h = (base + 8) & mask;
+    }
+    slot = 0xffffffffu;
+    return false;
+}
+__device__ __forceinline__ bool ghash_has(const uint32_t *G, uint32_t log, uint32_t x) {
+    uint32_t slot;
+    return ghash_find(G, log, x, slot);
 }
 
 // ---------------------------------------------------------------------------
@@ -258,6 +305,162 @@ __device__ __forceinline__ void heap_push_masked(uint64_t *h, uint32_t &sz, uint
     }
     sz += __popc(mask);
     __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Spilling queue of the large-budget kernels.  The shared-memory heap holds
+// the entries below a threshold tau; every entry >= tau sits, unsorted, in an
+// overflow array in the warp's global scratch.  So whenever the heap is not
+// empty its root is the minimum of the whole queue, and Algorithm 1's pop
+// order is unchanged.  A full heap moves its upper part out (tau drops to a
+// low quantile of 32 sampled entries); an empty heap takes the smallest
+// overflow entries back (tau rises to a sampled quantile, checked by a count
+// so that they fit).  Most discovered references are never popped, so the
+// overflow is touched rarely.
+// ---------------------------------------------------------------------------
+struct Spill {
+    uint64_t *B;   // overflow entries (global memory), unsorted, all >= tau
+    uint32_t nb;   // their count (identical in every lane)
+    uint64_t tau;  // heap entries < tau <= overflow entries; ~0 while nothing has spilled
+};
+
+// composite minimum of one 64-bit value per lane
+__device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    const uint32_t mh = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t ml = __reduce_min_sync(0xffffffffu, hi == mh ? lo : 0xffffffffu);
+    return ((uint64_t)mh << 32) | ml;
+}
+
+// restore the heap order below node i (all lanes take part)
+__device__ void heap_sift_down(uint64_t *h, uint32_t sz, uint32_t i) {
+    const int lane = lane_id();
+    const uint64_t v = h[i];
+    __syncwarp();
+    for (;;) {
+        const uint32_t c0 = 32 * i + 1;
+        if (c0 >= sz) break;
+        const uint32_t ci = c0 + lane;
+        const uint64_t cv = ci < sz ? h[ci] : ~0ull;
+        const uint64_t m = warp_min64(cv);
+        const int w = __ffs(__ballot_sync(0xffffffffu, cv == m)) - 1;
+        if (m >= v) break;
+        if (lane == w) h[i] = cv;
+        i = c0 + (uint32_t)w;
+    }
+    __syncwarp();
+    if (lane == 0) h[i] = v;
+    __syncwarp();
+}
+
+// bottom-up heap construction over h[0 .. sz)
+__device__ void heap_build(uint64_t *h, uint32_t sz) {
+    if (sz < 2) return;
+    for (int64_t i = (int64_t)(sz - 2) / 32; i >= 0; i--) heap_sift_down(h, sz, (uint32_t)i);
+}
+
+// move the heap's entries >= t (a low sampled quantile) to the overflow
+__device__ void spill_shrink(uint64_t *h, uint32_t &sz, Spill &sp) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1;
+    uint64_t smp[1] = {h[(uint32_t)(((uint64_t)lane * sz) >> 5)]};
+    reg_bitonic_sort_t<1, uint64_t>(smp);
+    const uint64_t t = __shfl_sync(0xffffffffu, smp[0], 12);  // an entry of the heap: at least it moves
+    uint32_t w = 0, nb = sp.nb;
+    for (uint32_t base = 0; base < sz; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < sz;
+        const uint64_t x = valid ? h[i] : ~0ull;
+        const bool keep = valid && x < t;
+        const unsigned mk = __ballot_sync(0xffffffffu, keep), mv = __ballot_sync(0xffffffffu, valid && !keep);
+        __syncwarp();
+        if (keep) h[w + __popc(mk & lt)] = x;  // in place: never past what this step read
+        if (valid && !keep) sp.B[nb + __popc(mv & lt)] = x;
+        w += __popc(mk);
+        nb += __popc(mv);
+        __syncwarp();
+    }
+    sz = w;
+    sp.nb = nb;
+    sp.tau = t;
+    heap_build(h, sz);
+}
+
+// the heap is empty: take the smallest overflow entries back (at most hcap)
+__device__ void spill_refill(uint64_t *h, uint32_t &sz, Spill &sp, uint32_t hcap) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1;
+    uint64_t t = ~0ull;  // everything fits: take it all
+    if (sp.nb > hcap) {
+        uint64_t smp[1] = {sp.B[(uint32_t)(((uint64_t)lane * sp.nb) >> 5)]};
+        reg_bitonic_sort_t<1, uint64_t>(smp);
+        int r = (int)((32u * (hcap / 2)) / sp.nb);  // the sample whose quantile is about hcap / 2 entries
+        if (r > 31) r = 31;
+        for (;;) {
+            t = __shfl_sync(0xffffffffu, smp[0], r) + 1;  // entries up to that sample move
+            uint32_t c = 0;
+            for (uint32_t i = lane; i < sp.nb; i += 32) c += sp.B[i] < t;
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (c <= hcap) break;
+            if (r == 0) {
+                uint64_t m = ~0ull;  // the exact minimum: one entry always fits
+                for (uint32_t i = lane; i < sp.nb; i += 32) m = min(m, sp.B[i]);
+                t = warp_min64(m) + 1;
+                break;
+            }
+            r >>= 1;
+        }
+    }
+    uint32_t na = 0, w = 0;
+    for (uint32_t base = 0; base < sp.nb; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < sp.nb;
+        const uint64_t x = valid ? sp.B[i] : ~0ull;
+        const bool in = valid && x < t;
+        const unsigned mi = __ballot_sync(0xffffffffu, in), mo = __ballot_sync(0xffffffffu, valid && !in);
+        __syncwarp();
+        if (in) h[na + __popc(mi & lt)] = x;
+        if (valid && !in) sp.B[w + __popc(mo & lt)] = x;  // compacted in place
+        na += __popc(mi);
+        w += __popc(mo);
+        __syncwarp();
+    }
+    sz = na;
+    sp.nb = w;
+    sp.tau = w == 0 ? ~0ull : t;
+    heap_build(h, sz);
+}
+
+template <bool SP>
+__device__ __forceinline__ void queue_pop(uint64_t *h, uint32_t &sz, Spill &sp, uint32_t hcap) {
+    heap_pop(h, sz);
+    if (SP && sz == 0 && sp.nb > 0) spill_refill(h, sz, sp, hcap);
+}
+
+// push the entries of the lanes in mask (pos = the lane's rank in mask)
+template <bool SP>
+__device__ __forceinline__ void queue_push(uint64_t *h, uint32_t &sz, Spill &sp, uint32_t hcap, uint64_t e,
+                                           unsigned mask, int pos) {
+    if (!SP) {
+        heap_push_masked(h, sz, e, mask, pos);
+        return;
+    }
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1;
+    const bool inm = (mask >> lane) & 1u;
+    unsigned ma = __ballot_sync(0xffffffffu, inm && e < sp.tau);
+    while (sz + __popc(ma) > hcap) {
+        spill_shrink(h, sz, sp);
+        ma = __ballot_sync(0xffffffffu, inm && e < sp.tau);
+    }
+    const unsigned mb = mask & ~ma;
+    if (mb) {
+        if ((mb >> lane) & 1u) sp.B[sp.nb + __popc(mb & lt)] = e;
+        sp.nb += __popc(mb);
+        __syncwarp();
+    }
+    if (ma) heap_push_masked(h, sz, e, ma, __popc(ma & lt));
+    if (sz == 0 && sp.nb > 0) spill_refill(h, sz, sp, hcap);
 }
 
 // ---------------------------------------------------------------------------
@@ -1006,6 +1209,7 @@ __device__ __forceinline__ void sort_parts(const uint32_t *D, uint8_t *rk, uint8
 // ---------------------------------------------------------------------------
 template <int DT, bool WIN, bool GRP>
 __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8_t *wscratch) {
+    constexpr bool SP = WIN;  // the large-budget kernels also spill the queue and the visited set
     const DevIndex &ix = A.ix;
     const WarpLayout &L = A.L;
     const int lane = lane_id();
@@ -1028,7 +1232,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     uint8_t *rk = smem + L.rank;
     uint8_t *sc = smem + L.sc;
     uint64_t *heap = (uint64_t *)(smem + L.heap);
-    uint32_t *H = (uint32_t *)(smem + L.hash);
+    uint32_t *H = SP ? (uint32_t *)(wscratch + A.hash_off) : (uint32_t *)(smem + L.hash);
+    Spill sp{SP ? (uint64_t *)(wscratch + A.spill_off) : nullptr, 0u, ~0ull};
     uint64_t *rbuf = (uint64_t *)(smem + L.rbuf);
     uint64_t *bkey = (uint64_t *)(smem + L.bkey);
     uint32_t *bidx = (uint32_t *)(smem + L.bidx);
@@ -1044,7 +1249,11 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         for (int c = lane; c < (vb >> 4); c += 32) dst[c] = __ldg(src + c);
     }
     // clear the visited set and the walk counters
-    for (uint32_t i = lane; i < (1u << L.hash_log); i += 32) H[i] = 0;
+    if (SP) {
+        for (uint32_t i = 4 * lane; i < (1u << L.hash_log); i += 128) *(uint4 *)(H + i) = make_uint4(0, 0, 0, 0);
+    } else {
+        for (uint32_t i = lane; i < (1u << L.hash_log); i += 32) H[i] = 0;
+    }
     if (lane < 16) misc[lane] = 0;
     __syncwarp();
 
@@ -1157,7 +1366,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
         int alen;
         if (take_ref) {
             uint32_t p = (uint32_t)top;
-            heap_pop(heap, hsz);
+            queue_pop<SP>(heap, hsz, sp, L.heap_cap);
             alen = R;
             if (p == nx_id) {
                 x = nx_row;
@@ -1194,7 +1403,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                 for (int e = lane; e < (int)wcnt * b; e += 32) {
                     uint32_t j = bidx[wstart + e / b];
                     int32_t r = __ldg(ix.brefs + (int64_t)j * b + (e % b));
-                    bool keep = r >= 0 && r < ix.N && !hash_has(H, L.hash_log, (uint32_t)r);
+                    bool keep = r >= 0 && r < ix.N &&
+                                !(SP ? ghash_has(H, L.hash_log, (uint32_t)r) : hash_has(H, L.hash_log, (uint32_t)r));
                     wref[e] = keep ? r : -1;
                 }
                 __syncwarp();
@@ -1234,7 +1444,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
             slot = nx_slot;
         } else {
             bool isnew = false;
-            if (lane < alen && x >= 0 && x < ix.N) isnew = !hash_find(H, L.hash_log, (uint32_t)x, slot);
+            if (lane < alen && x >= 0 && x < ix.N)
+                isnew = !(SP ? ghash_find(H, L.hash_log, (uint32_t)x, slot) : hash_find(H, L.hash_log, (uint32_t)x, slot));
             mask = __ballot_sync(0xffffffffu, isnew);
             int room = T - t;
             while (__popc(mask) > room) mask &= ~(1u << (31 - __clz(mask)));  // keep the first `room` in list order
@@ -1266,8 +1477,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                 }
             }
             mine = inm ? (((uint64_t)key << 32) | (uint32_t)x) : ~0ull;
-            heap_push_masked(heap, hsz, mine, mask, pos);
-            if ((int64_t)hsz + 1 > maxq) maxq = (int64_t)hsz + 1;
+            queue_push<SP>(heap, hsz, sp, L.heap_cap, mine, mask, pos);
+            if ((int64_t)hsz + sp.nb + 1 > maxq) maxq = (int64_t)hsz + sp.nb + 1;
         }
         // The next pop is known now.  When it is a reference, take its kNN row
         // (usually the speculative one) and start copying its unvisited
@@ -1289,7 +1500,8 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
                     uint32_t s2 = kNone;
                     bool nw = false;
                     if (lane < R && nx_row >= 0 && nx_row < ix.N)
-                        nw = !hash_find(H, L.hash_log, (uint32_t)nx_row, s2);
+                        nw = !(SP ? ghash_find(H, L.hash_log, (uint32_t)nx_row, s2)
+                                  : hash_find(H, L.hash_log, (uint32_t)nx_row, s2));
                     unsigned mk = __ballot_sync(0xffffffffu, nw);
                     const int room2 = T - (t + m);
                     while (__popc(mk) > room2) mk &= ~(1u << (31 - __clz(mk)));
@@ -1391,8 +1603,7 @@ __global__ void __launch_bounds__(192, 2) search_kernel(SearchArgs A) {
     extern __shared__ __align__(16) uint8_t smem_all[];
     const int warp = threadIdx.x >> 5;
     uint8_t *smem = smem_all + (size_t)warp * A.L.total;
-    uint8_t *wscratch =
-        WIN ? A.gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * (size_t)A.gcap * 24 : nullptr;
+    uint8_t *wscratch = WIN ? A.gscratch + ((size_t)blockIdx.x * (blockDim.x >> 5) + warp) * A.wstride : nullptr;
     const int64_t count = A.list_count ? (int64_t)*A.list_count : (A.list ? A.list_len : A.nq);
     if (A.ticket) {
         // persistent: pull queries from the device work queue

@@ -344,3 +344,26 @@ def test_persistent_plans_beyond_the_cache_limit_stay_correct(ann, tiny_sift):
         np.testing.assert_array_equal(ids.cpu().numpy(), want)
         assert np.all(st.cpu().numpy() == 0)
     ix.free()
+
+
+@pytest.mark.parametrize("dtype,P,n,R,d", [(np.uint8, 4, 16, 16, 128), (np.float32, 3, 16, 12, 96)])
+def test_large_budgets_spill_queue_and_visited_set(ann, dtype, P, n, R, d):
+    # budgets from 1024 on keep only 512 queue entries in shared memory, the
+    # rest of the queue and the visited set in global scratch; budgets up to
+    # the whole reachable set make the heap move entries out and take them
+    # back many times per query
+    N = 20000
+    X = gmm(500 + P, N, d, 12, dtype)
+    G, C, bg = build_oracle_index(X, P, n, R, 100, 5, 4, 5)
+    Q = gmm(501 + P, 48, d, 12, dtype)
+    rng = np.random.default_rng(7)
+    k = rng.choice([1, 10, 100], size=len(Q)).astype(np.int32)
+    T = rng.choice([1024, 1500, 3000, 6000, 8192], size=len(Q)).astype(np.int32)
+    for mode in (0, 1):
+        (wi, wk, wst), (gi, gk, gs, gst), _ = run_both(ann, X, G, C, bg, Q, k, T, 100, mode)
+        assert np.all(gs == 0)
+        np.testing.assert_array_equal(gi, wi)
+        assert_keys(gk, wk, dtype)
+        np.testing.assert_array_equal(gst[:, 0], wst["discovered"])
+        np.testing.assert_array_equal(gst[:, 1], wst["ref_pops"])
+        assert gst[:, 6].max() > 600          # queues longer than the shared-memory heap
