@@ -92,6 +92,14 @@ void free_plans(ann_index *ix);
 int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
                         int32_t kmax, int capT, int32_t *out_ids, void *out_keys, int32_t *out_status,
                         cudaStream_t stream);
+// plain launch over the queries listed in list[0 .. count) (device), sized for capT
+int search_launch_list(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
+                       int32_t kmax, int capT, const int32_t *list, int64_t count, int32_t *out_ids, void *out_keys,
+                       int32_t *out_status, cudaStream_t stream);
+// the persistent form's budget buckets: capacity 128 << b (capped at the largest budget)
+int search_bucket_of(int32_t T);
+int search_bucket_cap(int bucket);
+int search_num_buckets();
 // implemented in ann_knn_tc.cu: exact k-NN of uint8 rows on the tensor cores, d in {64, 128}, k <= 32
 int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_t nq, int d, int k,
                   int exclude_self, int32_t *out_ids, uint32_t *out_keys, cudaStream_t s);

@@ -460,6 +460,37 @@ int search_launch_plain(const ann_index *ix, const void *queries, int64_t nq, co
     return launch_search(A, capT, stream, false, nullptr, nullptr, nq, nullptr);
 }
 
+int search_launch_list(const ann_index *ix, const void *queries, int64_t nq, const int32_t *k, const int32_t *T,
+                       int32_t kmax, int capT, const int32_t *list, int64_t count, int32_t *out_ids, void *out_keys,
+                       int32_t *out_status, cudaStream_t stream) {
+    int r = device_props();
+    if (r != ANN_OK) return r;
+    if (nq == 0 || count == 0) return ANN_OK;
+    SearchArgs A{};
+    A.ix = ix->dev;
+    A.queries = queries;
+    A.nq = nq;
+    A.k = k;
+    A.T = T;
+    A.kmax = kmax;
+    A.out_ids = out_ids;
+    A.out_keys = out_keys;
+    A.out_status = out_status;
+    if (capT > kMaxT) capT = kMaxT;
+    if (capT < 32) capT = 32;
+    return launch_search(A, capT, stream, false, list, nullptr, count, nullptr);
+}
+
+int search_bucket_of(int32_t T) {
+    int b = 0;
+    while (b < kBuckets - 1 && T > (128 << b)) b++;
+    return b;
+}
+
+int search_bucket_cap(int bucket) { return bucket_cap(bucket); }
+
+int search_num_buckets() { return kBuckets; }
+
 }  // namespace ann
 
 using namespace ann;

@@ -333,7 +333,7 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 }
 
 // restore the heap order below node i (all lanes take part)
-__device__ void heap_sift_down(uint64_t *h, uint32_t sz, uint32_t i) {
+__device__ inline void heap_sift_down(uint64_t *h, uint32_t sz, uint32_t i) {
     const int lane = lane_id();
     const uint64_t v = h[i];
     __syncwarp();
@@ -354,13 +354,13 @@ __device__ void heap_sift_down(uint64_t *h, uint32_t sz, uint32_t i) {
 }
 
 // bottom-up heap construction over h[0 .. sz)
-__device__ void heap_build(uint64_t *h, uint32_t sz) {
+__device__ inline void heap_build(uint64_t *h, uint32_t sz) {
     if (sz < 2) return;
     for (int64_t i = (int64_t)(sz - 2) / 32; i >= 0; i--) heap_sift_down(h, sz, (uint32_t)i);
 }
 
 // move the heap's entries >= t (a low sampled quantile) to the overflow
-__device__ void spill_shrink(uint64_t *h, uint32_t &sz, Spill &sp) {
+__device__ inline void spill_shrink(uint64_t *h, uint32_t &sz, Spill &sp) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1;
     uint64_t smp[1] = {h[(uint32_t)(((uint64_t)lane * sz) >> 5)]};
@@ -387,7 +387,7 @@ __device__ void spill_shrink(uint64_t *h, uint32_t &sz, Spill &sp) {
 }
 
 // the heap is empty: take the smallest overflow entries back (at most hcap)
-__device__ void spill_refill(uint64_t *h, uint32_t &sz, Spill &sp, uint32_t hcap) {
+__device__ inline void spill_refill(uint64_t *h, uint32_t &sz, Spill &sp, uint32_t hcap) {
     const int lane = lane_id();
     const unsigned lt = (1u << lane) - 1;
     uint64_t t = ~0ull;  // everything fits: take it all

@@ -4,8 +4,10 @@
 // Submitted requests wait in a FIFO.  A host thread admits as many waiting
 // requests as fit both a free stream slot and the device scratch pool
 // (inputs + outputs of the merged batch), packs their queries into one pinned
-// staging buffer, and launches copy-in, Algorithm 1 (plain form) and
-// copy-out on the slot's stream.  Batches on different slots overlap on the
+// staging buffer, sorts them on the host into the persistent form's budget
+// buckets, and launches copy-in, one Algorithm 1 launch per non-empty bucket
+// (each sized for its own budget, largest first) and copy-out on the slot's
+// stream.  Batches on different slots overlap on the
 // GPU; requests that arrive while others run are admitted as soon as a slot
 // and scratch free up.  Completion is signalled by a host function enqueued
 // behind the copy-out (no device-side waiting).  Each query's result does not
@@ -120,7 +122,7 @@ namespace ann {
 
 static size_t batch_bytes(const ann_server *s, int64_t nq, int32_t kmax) {
     size_t a = ((size_t)nq * s->vbytes + 255) & ~size_t(255);
-    a += ((size_t)nq * 8 + 255) & ~size_t(255);              // k, T
+    a += ((size_t)nq * 12 + 255) & ~size_t(255);             // k, T, query order by bucket
     a += ((size_t)nq * kmax * 8 + 255) & ~size_t(255);       // ids, keys
     a += ((size_t)nq * 4 + 255) & ~size_t(255);              // status
     return a;
@@ -140,10 +142,8 @@ static bool launch_batch(ann_server *S, Slot &sl, std::vector<std::shared_ptr<Re
     size_t qo = 0;
     int32_t *hk = (int32_t *)(h + (size_t)kServeMaxBatch * vb);
     int32_t *hT = hk + kServeMaxBatch;
+    int32_t *hl = hT + kServeMaxBatch;  // batch positions grouped by budget bucket
     int32_t at = 0;
-    int32_t capT = 0;
-    for (auto &r : batch)
-        for (int32_t v : r->T) capT = std::max(capT, v);
     for (auto &r : batch) {
         memcpy(h + qo, r->queries.data(), (size_t)r->nq * vb);
         qo += (size_t)r->nq * vb;
@@ -151,12 +151,21 @@ static bool launch_batch(ann_server *S, Slot &sl, std::vector<std::shared_ptr<Re
         memcpy(hT + at, r->T.data(), 4 * (size_t)r->nq);
         at += r->nq;
     }
+    const int nb = search_num_buckets();
+    std::vector<int32_t> bstart(nb + 1, 0), bfill(nb, 0);
+    for (int32_t i = 0; i < nq; i++) bstart[search_bucket_of(hT[i]) + 1]++;
+    for (int b = 0; b < nb; b++) bstart[b + 1] += bstart[b];
+    for (int32_t i = 0; i < nq; i++) {
+        const int b = search_bucket_of(hT[i]);
+        hl[bstart[b] + bfill[b]++] = i;
+    }
     uint8_t *d = S->pool_base + off;
     uint8_t *dq = d;
     size_t o = ((size_t)nq * vb + 255) & ~size_t(255);
     int32_t *dk = (int32_t *)(d + o);
     int32_t *dT = dk + nq;
-    o += ((size_t)nq * 8 + 255) & ~size_t(255);
+    int32_t *dl = dT + nq;
+    o += ((size_t)nq * 12 + 255) & ~size_t(255);
     int32_t *dids = (int32_t *)(d + o);
     uint32_t *dkeys = (uint32_t *)(dids + (size_t)nq * kmax);
     o += ((size_t)nq * kmax * 8 + 255) & ~size_t(255);
@@ -164,9 +173,12 @@ static bool launch_batch(ann_server *S, Slot &sl, std::vector<std::shared_ptr<Re
     cudaStream_t s = sl.stream;
     bool ok = cudaMemcpyAsync(dq, h, (size_t)nq * vb, cudaMemcpyHostToDevice, s) == cudaSuccess &&
               cudaMemcpyAsync(dk, hk, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess &&
-              cudaMemcpyAsync(dT, hT, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess;
-    if (ok)
-        ok = search_launch_plain(S->index, dq, nq, dk, dT, kmax, capT, dids, dkeys, dst, s) == ANN_OK;
+              cudaMemcpyAsync(dT, hT, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+              cudaMemcpyAsync(dl, hl, 4 * (size_t)nq, cudaMemcpyHostToDevice, s) == cudaSuccess;
+    for (int b = nb - 1; ok && b >= 0; b--)
+        if (bstart[b + 1] > bstart[b])
+            ok = search_launch_list(S->index, dq, nq, dk, dT, kmax, search_bucket_cap(b), dl + bstart[b],
+                                    bstart[b + 1] - bstart[b], dids, dkeys, dst, s) == ANN_OK;
     uint8_t *ho = sl.h_out;
     if (ok)
         ok = cudaMemcpyAsync(ho, dids, (size_t)nq * kmax * 8, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
@@ -292,7 +304,7 @@ extern "C" int ann_server_create(const ann_index *index, size_t scratch_bytes, i
     for (int i = 0; i < max_streams; i++) {
         std::unique_ptr<Slot> sl(new Slot());
         sl->cv = &S->cv;
-        size_t in_b = (size_t)kServeMaxBatch * (S->vbytes + 8);
+        size_t in_b = (size_t)kServeMaxBatch * (S->vbytes + 12);
         size_t out_b = (size_t)kServeMaxBatch * (kMaxK * 8 + 4);
         if ((e = cudaStreamCreateWithFlags(&sl->stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaHostAlloc((void **)&sl->h_in, in_b, cudaHostAllocDefault)) != cudaSuccess ||
