@@ -250,7 +250,13 @@ enum {
  * k_all / T_all for every query.  kmax >= every k.  Outputs (device,
  * caller-owned): out_ids int32[nq*kmax] ascending by (key, id), padded with
  * -1; out_keys (optional) nq*kmax keys padded with UINT32_MAX / +inf;
- * out_status (optional) int32[nq] with ANN_OK or ANN_ERR_CAPACITY;
+ * out_status (optional) int32[nq], per query: ANN_OK; ANN_ERR_ARG for a
+ * per-query k outside [0, kmax] or T outside [0, 8192] (that query's output
+ * is all padding; the others are unaffected); ANN_ERR_CAPACITY if a bridge
+ * window could not be split below its buffer, which a valid index never
+ * causes (bridge ids are distinct, so every (key, rank tuple) composite
+ * names one bridge and halving a window always separates them: the check
+ * only guards against a corrupted index).
  * out_stats (optional) int64[nq*ANN_NSTATS].
  * mode ANN_MODE_PLAIN: one kernel launch for this batch on `stream`, sized
  * for the largest budget (per-query T costs one device max and a host sync).

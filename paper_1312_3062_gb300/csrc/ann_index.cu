@@ -312,6 +312,34 @@ __global__ void bg_goff_kernel(const uint32_t *ubid, const uint32_t *gstart, int
     goff[a] = (uint32_t)lo;
 }
 
+// suffix-major order: key s * nA + a of every bridge (a = prefix, s = suffix)
+__global__ void bg_skey_kernel(const uint32_t *ubid, int64_t M, uint32_t suf, uint32_t nA, uint32_t *key,
+                               uint32_t *pos) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    key[j] = (ubid[j] % suf) * nA + ubid[j] / suf;
+    pos[j] = (uint32_t)j;
+}
+
+__global__ void bg_sleaf_kernel(const uint32_t *skey, int64_t M, uint32_t nA, uint32_t *sleaf) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    sleaf[j] = skey[j] % nA;
+}
+
+// offS[s] = first suffix-major entry whose suffix is >= s  (s in [0, nS])
+__global__ void bg_offs_kernel(const uint32_t *skey, int64_t M, uint32_t nA, int64_t nS, uint32_t *offS) {
+    int64_t sfx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (sfx > nS) return;
+    int64_t lo = 0, hi = M;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)(skey[mid] / nA) < sfx) lo = mid + 1;
+        else hi = mid;
+    }
+    offS[sfx] = (uint32_t)lo;
+}
+
 __global__ void mark_refs_kernel(const int32_t *brefs, int64_t total, uint8_t *mark) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= total) return;
@@ -381,7 +409,40 @@ static int finish_bridge_index(ann_index *ix, DBuf<uint32_t> &ubid, int64_t M, c
         bg_goff_kernel<<<nblk(dv.nA + 1), 256, 0, s>>>(ubid.p, gstart.p, G, suf, dv.nA, goff.p);
         ANN_CUDA(cudaGetLastError());
     }
+    // suffix-major copy for the split walks (indexes without the group level)
+    DBuf<uint32_t> bmS, offS, sleaf, sidx;
+    const int64_t nS = suf;
+    if (G == 0 && M > 0) {
+        DBuf<uint32_t> k0, k1, v0;
+        ANN_CUDA_ALLOC(k0, M);
+        ANN_CUDA_ALLOC(k1, M);
+        ANN_CUDA_ALLOC(v0, M);
+        ANN_CUDA_ALLOC(sidx, M);
+        ANN_CUDA_ALLOC(sleaf, M);
+        ANN_CUDA_ALLOC(offS, nS + 1);
+        ANN_CUDA_ALLOC(bmS, (nS + 31) / 32);
+        bg_skey_kernel<<<nblk(M), 256, 0, s>>>(ubid.p, M, suf, (uint32_t)dv.nA, k0.p, v0.p);
+        size_t tb = 0;
+        ANN_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, k0.p, k1.p, v0.p, sidx.p, M, 0, 32, s));
+        DBuf<uint8_t> temp;
+        ANN_CUDA_ALLOC(temp, tb);
+        ANN_CUDA(cub::DeviceRadixSort::SortPairs(temp.p, tb, k0.p, k1.p, v0.p, sidx.p, M, 0, 32, s));
+        bg_sleaf_kernel<<<nblk(M), 256, 0, s>>>(k1.p, M, (uint32_t)dv.nA, sleaf.p);
+        bg_offs_kernel<<<nblk(nS + 1), 256, 0, s>>>(k1.p, M, (uint32_t)dv.nA, nS, offS.p);
+        bg_bits_kernel<<<nblk((nS + 31) / 32), 256, 0, s>>>(offS.p, nS, bmS.p);
+        ANN_CUDA(cudaGetLastError());
+        ANN_CUDA(cudaStreamSynchronize(s));
+    }
     ANN_CUDA(cudaStreamSynchronize(s));
+    ix->bmS = bmS.release();
+    ix->offS = offS.release();
+    ix->sleaf = sleaf.release();
+    ix->sidx = sidx.release();
+    dv.nS = nS;
+    dv.bmS = ix->bmS;
+    dv.offS = ix->offS;
+    dv.sleaf = ix->sleaf;
+    dv.sidx = ix->sidx;
     ix->leaf = leaf.release();
     ix->offA = offA.release();
     ix->bmA = bmA.release();
@@ -549,6 +610,10 @@ static void destroy(ann_index *ix) {
     cudaFree(ix->goff);
     cudaFree(ix->gstart);
     cudaFree(ix->gc2);
+    cudaFree(ix->bmS);
+    cudaFree(ix->offS);
+    cudaFree(ix->sleaf);
+    cudaFree(ix->sidx);
     delete ix;
 }
 
@@ -709,7 +774,8 @@ extern "C" int ann_index_get_info(const ann_index *index, ann_index_info *out) {
     out->bytes_vectors = (int64_t)(dv.N * dv.d * es);
     out->bytes_graph = dv.N * dv.R * 4;
     out->bytes_bridges = dv.M * (4 + 4 * dv.b) + (dv.nA + 1) * 4 + (dv.nA + 31) / 32 * 4 +
-                         (dv.ngroups ? (dv.ngroups + 1) * 4 + dv.ngroups + (dv.nA + 1) * 4 : 0);
+                         (dv.ngroups ? (dv.ngroups + 1) * 4 + dv.ngroups + (dv.nA + 1) * 4 : 0) +
+                         (dv.sidx ? dv.M * 8 + (dv.nS + 1) * 4 + (dv.nS + 31) / 32 * 4 : 0);
     out->groups = dv.ngroups;
     return ANN_OK;
 }

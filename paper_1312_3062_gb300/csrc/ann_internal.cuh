@@ -66,6 +66,13 @@ struct DevIndex {
     const uint32_t *goff;   // nA+1
     const uint32_t *gstart; // ngroups+1
     const uint8_t *gc2;     // ngroups
+    // suffix-major copy (indexes without the group level): the same bridges
+    // sorted by (suffix s, prefix a); per suffix node a presence bit (bmS)
+    // and a CSR range (offS, nS + 1 entries); per bridge its prefix a (sleaf)
+    // and its position in the prefix-major order (sidx).  nS = n^(P-PA);
+    // sidx == nullptr when absent.
+    int64_t nS;
+    const uint32_t *bmS, *offS, *sleaf, *sidx;
 };
 
 }  // namespace ann
@@ -80,6 +87,7 @@ struct ann_index {
     int32_t *brefs;
     uint32_t *goff, *gstart;
     uint8_t *gc2;
+    uint32_t *bmS, *offS, *sleaf, *sidx;
     int64_t bridged_refs;
     // cached persistent-mode plans (see ann_search.cu)
     void *plans;

@@ -68,8 +68,8 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
     L.tabD = o;   o = align_up(o + 4u * P * n, 16);
     L.rank = o;   o = align_up(o + (uint32_t)P * n, 16);
-    L.sk = 0;     // sorted keys of the prefix parts are read as D[sc[r]]
-    L.sc = o;     o = align_up(o + (uint32_t)PA * n, 16);
+    L.sk = 0;     // sorted keys are read as D[sc[r]]
+    L.sc = o;     o = align_up(o + (uint32_t)P * n, 16);  // center id at each rank, every part
     uint32_t lpn = 1;
     while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
     const uint32_t qcap = spill && (uint32_t)capT > kSpillHeap ? kSpillHeap : (uint32_t)capT;
@@ -653,6 +653,178 @@ struct WalkState {
     int gbuf;             // which of the two scratch buffers holds it
 };
 
+// exclusive prefix sum over pref[0 .. n) in place, total in pref[n]
+__device__ __forceinline__ void warp_exclusive_scan(uint32_t *pref, int n) {
+    const int lane = lane_id();
+    const int per = (n + 31) / 32;
+    uint32_t local = 0;
+    for (int i = 0; i < per; i++) {
+        int r = lane * per + i;
+        if (r < n) local += pref[r];
+    }
+    uint32_t incl = local;
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    uint32_t run = incl - local;
+    __syncwarp();
+    for (int i = 0; i < per; i++) {
+        int r = lane * per + i;
+        if (r < n) {
+            uint32_t v = pref[r];
+            pref[r] = run;
+            run += v;
+        }
+    }
+    if (lane == 31) pref[n] = incl;
+    __syncwarp();
+}
+
+// Second pass of a split walk (indexes with the suffix-major copy).  A bridge
+// with prefix key A and suffix key B lies at or below hi only if A <= theta
+// or B < hi - theta; the first pass read every bridge whose prefix bound is
+// <= theta, so this pass lists the suffix nodes s with lower bound
+// B(s) <= bound2 and keeps, of their bridges, only those whose prefix bound
+// exceeds theta -- each bridge is read by exactly one pass that can emit it.
+template <int DT>
+__device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
+                            uint64_t hi, uint32_t theta, uint32_t bound2, uint64_t *okey, uint32_t *oval,
+                            uint32_t ocap, int64_t &nodes_here, int64_t &leaves_here) {
+    const int lane = lane_id();
+    const int n = ix.n, P = ix.P, PA = ix.PA, q0 = ix.PA, nsuf = P - PA;
+    const uint32_t *D = (const uint32_t *)(smem + L.tabD);
+    const uint8_t *rk = smem + L.rank;
+    const uint8_t *sc = smem + L.sc;
+    auto sk = [&](int p, int r) -> uint32_t { return D[p * n + sc[p * n + r]]; };
+    uint32_t *pref = (uint32_t *)(smem + L.pref);
+    uint32_t *nodes = (uint32_t *)(smem + L.nodes);  // 4 words per node: start, count, key bound, (s << 16) | ranks
+    uint32_t *cnt = (uint32_t *)(smem + L.misc);
+    const uint32_t hik = (uint32_t)(hi >> 32), lok = (uint32_t)(lo >> 32);
+    const bool pow2n = (n & (n - 1)) == 0;
+    const int logn = 31 - __clz(n);
+    // candidate ranks of the second suffix part per rank of the first
+    for (int r = lane; r < n; r += 32) {
+        uint32_t c;
+        if (nsuf == 1) {
+            c = sk(q0, r) <= bound2 ? 1u : 0u;
+        } else {
+            const uint32_t b0 = sk(q0, r);
+            if (KeyOps<DT>::add_lo(b0, sk(q0 + 1, 0)) > bound2) {
+                c = 0;
+            } else {
+                int lo1 = 1, hi1 = n;
+                while (lo1 < hi1) {
+                    const int mid = (lo1 + hi1 + 1) >> 1;
+                    if (KeyOps<DT>::add_lo(b0, sk(q0 + 1, mid - 1)) <= bound2) lo1 = mid;
+                    else hi1 = mid - 1;
+                }
+                c = (uint32_t)lo1;
+            }
+        }
+        pref[r] = c;
+    }
+    __syncwarp();
+    warp_exclusive_scan(pref, n);
+    const uint32_t total = pref[n];
+    uint32_t nl = 0;
+    int rp = 0;
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t f = base + lane;
+        bool ok = false;
+        uint32_t node = 0, kb = 0, rs = 0;
+        if (f < total) {
+            while (rp + 1 < n && pref[rp + 1] <= f) rp++;
+            const int r2 = rp, r3 = (int)(f - pref[r2]);
+            const uint32_t c2 = sc[q0 * n + r2];
+            if (nsuf == 1) {
+                node = c2;
+                kb = D[q0 * n + c2];
+                rs = (uint32_t)r2;
+            } else {
+                const uint32_t c3 = sc[(q0 + 1) * n + r3];
+                node = c2 * n + c3;
+                kb = KeyOps<DT>::add_lo(D[q0 * n + c2], D[(q0 + 1) * n + c3]);
+                rs = ((uint32_t)r2 << 8) | (uint32_t)r3;
+            }
+            ok = (__ldg(ix.bmS + (node >> 5)) >> (node & 31)) & 1u;
+        }
+        nodes_here += (f < total);
+        const unsigned m = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            const uint32_t pos = nl + __popc(m & ((1u << lane) - 1));
+            const uint32_t j0 = __ldg(ix.offS + node), j1 = __ldg(ix.offS + node + 1);
+            nodes[4 * pos + 0] = j0;
+            nodes[4 * pos + 1] = j1 - j0;
+            nodes[4 * pos + 2] = kb;
+            nodes[4 * pos + 3] = (node << 16) | rs;
+        }
+        nl += __popc(m);
+        const bool flush = (nl + 32 > L.ncap) || (base + 32 >= total);
+        if (!flush || nl == 0) continue;
+        __syncwarp();
+        uint32_t run = 0;
+        for (uint32_t b0 = 0; b0 < nl; b0 += 32) {
+            const uint32_t i = b0 + lane;
+            const uint32_t c = i < nl ? nodes[4 * i + 1] : 0;
+            uint32_t incl = c;
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            if (i < nl) nodes[4 * i + 1] = run + incl - c;  // flat start of node i
+            run += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        __syncwarp();
+        uint32_t np = 0;
+        for (uint32_t g = lane; g < run; g += 32) {
+            while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
+            const uint32_t jj = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
+            const uint32_t a = __ldg(ix.sleaf + jj);
+            const uint32_t c0 = PA == 1 ? a : (pow2n ? (a >> logn) : a / n);
+            const uint32_t c1 = PA == 1 ? 0u : a - c0 * n;
+            const uint32_t kA = PA == 1 ? D[c0] : KeyOps<DT>::add_lo(D[c0], D[n + c1]);
+            if (kA <= theta) continue;  // the first pass owns it
+            const uint32_t kb = nodes[4 * np + 2], sw = nodes[4 * np + 3], sfx = sw >> 16;
+            uint32_t key = KeyOps<DT>::add_lo(kA, kb);
+            if (key > hik) continue;
+            if (DT == ANN_F32) {
+                if (!first && KeyOps<DT>::add_hi(KeyOps<DT>::up(kA), KeyOps<DT>::up(kb)) < lok) continue;
+                uint32_t d0, d1, d2 = 0u, d3 = 0u;
+                d0 = D[c0];
+                if (PA == 1) {
+                    d1 = D[n + sfx];
+                } else {
+                    d1 = D[n + c1];
+                    if (nsuf == 1) {
+                        d2 = D[2 * n + sfx];
+                    } else {
+                        const uint32_t c2 = pow2n ? (sfx >> logn) : sfx / n;
+                        d2 = D[2 * n + c2];
+                        d3 = D[3 * n + (sfx - c2 * n)];
+                    }
+                }
+                key = KeyOps<DT>::sum4(d0, d1, d2, d3);
+                if (key > hik) continue;
+            }
+            if (!first && key < lok) continue;
+            const uint32_t rpre = PA == 1 ? (uint32_t)rk[c0] : (((uint32_t)rk[c0] << 8) | rk[n + c1]);
+            const uint32_t ranks = (rpre << (8 * nsuf)) | (sw & 0xffffu);
+            const uint64_t comp = ((uint64_t)key << 32) | ranks;
+            if (comp <= hi && (first || comp > lo)) {
+                const uint32_t slot = atomicAdd(&cnt[0], 1u);
+                if (slot < ocap) {
+                    okey[slot] = comp;
+                    oval[slot] = __ldg(ix.sidx + jj);
+                }
+            }
+        }
+        leaves_here += run;
+        nl = 0;
+        __syncwarp();
+    }
+}
+
 // Emit the composite (key << 32 | packed ranks) of every non-empty bridge with
 // lo < composite <= hi (lo ignored when first).  Returns how many there were;
 // only the first ocap are stored.  Two phases per chunk: (1) the prefix
@@ -684,20 +856,54 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     uint32_t *glist = (uint32_t *)(smem + L.glist);  // 5 words per group: start, count, kpre, D2, ranks
     const int nsuf = P - PA;
     if (lane == 0) cnt[0] = 0;
+    // Split walk (suffix-major copy present): the first pass lists the prefix
+    // nodes with bound A <= theta, the second (walk_suffix) the suffix nodes
+    // with bound B <= bound2, so that A + B <= hi is covered by one of them;
+    // theta splits the window's excess over the smallest possible A + B in
+    // proportion to the parts on each side.  Otherwise one pass lists the
+    // prefix nodes with A + min B <= hi.
+    const bool split = !GRP && ix.sidx != nullptr;
+    uint32_t theta = 0, bound2 = 0;
+    bool pass2 = false;
+    if (split) {
+        const uint32_t minA = PA == 1 ? sk(0) : KeyOps<DT>::add_lo(sk(0), sk(n));
+        if (DT == ANN_U8) {
+            int64_t ex = (int64_t)hik - (int64_t)minA - (int64_t)msuf;
+            if (ex < 0) ex = 0;
+            int64_t th = (int64_t)minA + ex * PA / P;
+            if (th > (int64_t)hik) th = hik;
+            theta = (uint32_t)th;
+            const int64_t b2 = (int64_t)hik - th - 1;  // integers: A > theta and A + B <= hi give B <= hi - theta - 1
+            pass2 = b2 >= 0;
+            bound2 = pass2 ? (uint32_t)b2 : 0u;
+        } else {
+            const float h = __uint_as_float(hik), a = __uint_as_float(minA), m = __uint_as_float(msuf);
+            const float ex = fmaxf(h - a - m, 0.f);
+            const float th = fminf(a + ex * (float)PA / (float)P, h);
+            theta = __float_as_uint(th);
+            // the key rounds the exact sum, so A + B < nextup(hi) when the key is <= hi
+            const float b2 = __fsub_ru(__uint_as_float(f32_next_up(hik)), th);
+            pass2 = b2 >= 0.f;
+            bound2 = pass2 ? __float_as_uint(b2) : 0u;
+        }
+    }
+    auto admitA = [&](uint32_t kA) -> bool {
+        return split ? kA <= theta : KeyOps<DT>::add_lo(kA, msuf) <= hik;
+    };
     // candidate part-1 ranks per r0 (PA == 2), or 0/1 per r0 (PA == 1)
     for (int r0 = lane; r0 < n; r0 += 32) {
         uint32_t c;
         if (PA == 1) {
-            c = KeyOps<DT>::add_lo(sk(r0), msuf) <= hik ? 1u : 0u;
+            c = admitA(sk(r0)) ? 1u : 0u;
         } else {
             uint32_t a0 = sk(r0);
-            if (KeyOps<DT>::add_lo(KeyOps<DT>::add_lo(a0, sk(n)), msuf) > hik) {
+            if (!admitA(KeyOps<DT>::add_lo(a0, sk(n)))) {
                 c = 0;
             } else {
                 int lo1 = 1, hi1 = n;  // answer in [1, n]
                 while (lo1 < hi1) {
                     int mid = (lo1 + hi1 + 1) >> 1;
-                    if (KeyOps<DT>::add_lo(KeyOps<DT>::add_lo(a0, sk(n + mid - 1)), msuf) <= hik) lo1 = mid;
+                    if (admitA(KeyOps<DT>::add_lo(a0, sk(n + mid - 1)))) lo1 = mid;
                     else hi1 = mid - 1;
                 }
                 c = (uint32_t)lo1;
@@ -706,32 +912,7 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
         pref[r0] = c;
     }
     __syncwarp();
-    // exclusive prefix sum over pref[0..n): chunked warp scan
-    {
-        const int per = (n + 31) / 32;
-        uint32_t local = 0;
-        for (int i = 0; i < per; i++) {
-            int r = lane * per + i;
-            if (r < n) local += pref[r];
-        }
-        uint32_t incl = local;
-        for (int off = 1; off < 32; off <<= 1) {
-            uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += v;
-        }
-        uint32_t run = incl - local;
-        __syncwarp();
-        for (int i = 0; i < per; i++) {
-            int r = lane * per + i;
-            if (r < n) {
-                uint32_t v = pref[r];
-                pref[r] = run;
-                run += v;
-            }
-        }
-        if (lane == 31) pref[n] = incl;
-        __syncwarp();
-    }
+    warp_exclusive_scan(pref, n);
     const uint32_t total = pref[n];
     int64_t nodes_here = 0, leaves_here = 0;
     uint32_t nl = 0;      // listed nodes (warp-uniform)
@@ -931,6 +1112,9 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
             __syncwarp();
         }
     }
+    __syncwarp();
+    if (!GRP && split && pass2)
+        walk_suffix<DT>(ix, smem, L, lo, first, hi, theta, bound2, okey, oval, ocap, nodes_here, leaves_here);
     __syncwarp();
     for (int off = 16; off > 0; off >>= 1) nodes_here += __shfl_xor_sync(0xffffffffu, nodes_here, off);
     if (lane == 0) {
@@ -1173,7 +1357,7 @@ __device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_
         if (r < n) {
             const uint32_t c = (uint32_t)(v[s] & (PACK ? 0xffu : 0xffffffffu));
             rk[p * n + c] = (uint8_t)r;
-            if (p < PA) sc[p * n + r] = (uint8_t)c;
+            sc[p * n + r] = (uint8_t)c;
         }
     }
     first_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> SH);

@@ -367,3 +367,28 @@ def test_large_budgets_spill_queue_and_visited_set(ann, dtype, P, n, R, d):
         np.testing.assert_array_equal(gst[:, 0], wst["discovered"])
         np.testing.assert_array_equal(gst[:, 1], wst["ref_pops"])
         assert gst[:, 6].max() > 600          # queues longer than the shared-memory heap
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_invalid_per_query_parameters_fail_alone(ann, tiny_sift, mode):
+    # a per-query k above kmax or below 0, or a budget below 0 or above the
+    # largest one, fails that query alone (ANN_ERR_ARG, all padding); every
+    # other query of the batch equals the oracle bit for bit
+    X, Q, G, C, bg = tiny_sift
+    Qs = Q[:48]
+    k = np.full(len(Qs), 10, np.int32)
+    T = np.full(len(Qs), 300, np.int32)
+    k[3], T[17], T[30], k[41] = 11, -1, 9000, -2
+    bad = np.zeros(len(Qs), bool)
+    bad[[3, 17, 30, 41]] = True
+    ix = ann.Index.create(dev(X), dev(G), dev(C), b=5, bridges=bg)
+    ids, keys, st = ann.ann_search_batch(ix, dev(Qs), dev(k), dev(T), kmax=10, mode=mode)
+    torch.cuda.synchronize()
+    st = st.cpu().numpy()
+    ids, keys = ids.cpu().numpy(), gpu_keys(keys, X.dtype)
+    np.testing.assert_array_equal(st, np.where(bad, ann.ANN_ERR_ARG, ann.ANN_OK))
+    assert np.all(ids[bad] == -1) and np.all(np.isinf(keys[bad]))
+    wi, wk, _ = oracle.search(X, G, C, bg, Qs[~bad], 10, 300, kmax=10, nthreads=8)
+    np.testing.assert_array_equal(ids[~bad], wi)
+    np.testing.assert_array_equal(keys[~bad], wk)
+    ix.free()
