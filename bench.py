@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--knn-approx", action="store_true",
                     help="workload 2 or 5: approximate kNN graph versus the exact one (build time, graph "
                          "recall; on workload 2 also the search each graph gives)")
+    ap.add_argument("--adc", action="store_true",
+                    help="Graph-D-ADC (Sec. 5.4) on the SIFT-shaped 10M mixture: recall@{1,10,100} of the true "
+                         "nearest neighbour and ms/query versus list length L, m = 8 and 16 bytes per code")
     ap.add_argument("--workload", type=int, default=5, choices=[2, 3, 4, 5],
                     help="5 sift10m served (default, the headline); 2 sift1m; 3 gist1m uneven k/T; "
                          "4 hog4m recall-vs-T")
@@ -335,7 +338,14 @@ def oracle_sample_qps(torch, ann, W, T, budget_s=12.0):
         passes += 1
         done += len(Qh)
     el = time.perf_counter() - t0
-    return done / el, cores, len(Qh), passes, el
+    # one thread, on a prefix of the queries (about a tenth of the budget)
+    n1, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < budget_s / 10 and n1 < len(Qh):
+        m = min(64, len(Qh) - n1)
+        oracle.search(X, G, C, bg, Qh[n1:n1 + m], K, T, kmax=K, nthreads=1)
+        n1 += m
+    qps1 = n1 / (time.perf_counter() - t1)
+    return done / el, cores, len(Qh), passes, el, qps1, n1
 
 
 def host_bridges(index):
@@ -402,6 +412,8 @@ def main():
 
     if args.knn_approx:
         return run_knn_approx(args, rank, ws, log, torch, ann, datagen)
+    if args.adc:
+        return run_adc(args, rank, ws, log, torch, ann, datagen)
     W = build_workload(args, torch, ann, datagen, log)
     if args.build_only:
         torch.cuda.synchronize()
@@ -541,11 +553,12 @@ def measure(args, rank, ws, log, torch, ann, datagen, W, headline):
     cpu_baseline = None
     if headline and not args.no_cpu_baseline and rank == 0 and ws == 1:
         index_host_copies(torch, ann, W)
-        qps, cores, n2, passes, el = oracle_sample_qps(torch, ann, W, T90)
+        qps, cores, n2, passes, el, qps1, n1 = oracle_sample_qps(torch, ann, W, T90)
         cpu_baseline = {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
                         "sample": f"{passes} pass(es) over {n2} queries of the same workload at T={T90}, k=10, "
                                   f"one query per thread, {el:.1f}s; search only, on the index arrays the GPU "
-                                  f"built"}
+                                  f"built",
+                        "single_thread": {"value": qps1, "unit": "queries/s", "sample": f"the first {n1} queries"}}
 
     line = {
         "metric": METRIC,
@@ -822,6 +835,77 @@ def run_knn_approx(args, rank, ws, log, torch, ann, datagen):
             ix.free()
         log(f"approx {e}")
         out["settings"].append(e)
+    print(json.dumps(out), flush=True)
+
+
+def run_adc(args, rank, ws, log, torch, ann, datagen):
+    """Graph-D-ADC (Sec. 5.4, Table 2's metric) on the SIFT-shaped 10M mixture
+    standing in for BIGANN: K = 10,000 coarse centers (seeded data rows),
+    each reference listed under its exact nearest center, residuals product
+    quantized with m parts of 256 codewords (GPU k-means on a 1M-row sample
+    of residuals), the lists of a query found by Algorithm 1 over a GPU index
+    of the centers (P = 2 x n = 128, kNN graph R = 16), the first L members
+    re-ranked by asymmetric distance.  recall@R = share of queries whose true
+    nearest neighbour is among the top R (Table 2's recall@T); ms/query =
+    one whole 10,000-query batch (coarse search + re-ranking, CUDA events,
+    L2 flushed) / queries."""
+    if rank != 0:
+        return
+    spec = datagen.WORKLOADS[5]
+    N = args.N or spec["N"]
+    nq = args.nq or spec["nq"]
+    K = 10_000 if N >= 1_000_000 else max(16, N // 1000)
+    t0 = time.time()
+    X = torch.from_numpy(datagen.references(5, N)).cuda()
+    Q = torch.from_numpy(datagen.queries(5, nq)).cuda()
+    d = X.shape[1]
+    Cc = X[torch.from_numpy(datagen.coarse_rows(5, N, K)).cuda()].contiguous()
+    Cf = Cc.to(torch.float32)
+    a_ids, _ = ann.ann_exact_knn(Cc, X, 1)
+    assign = a_ids[:, 0].contiguous()
+    order = torch.sort(assign.long(), stable=True)
+    members = order.indices.to(torch.int32).contiguous()
+    offsets = torch.zeros(K + 1, dtype=torch.int64, device="cuda")
+    offsets[1:] = torch.cumsum(torch.bincount(assign.long(), minlength=K), 0)
+    gt, _ = ann.ann_exact_knn(X, Q, 1)
+    gt = gt[:, 0].long()
+    Gc, _ = ann.ann_build_knn_graph(Cc, 16)
+    pc = ann.ann_train_centers(Cc, 2, 128, 10, datagen.kmeans_init_rows(5, K, 128))
+    ixc = ann.Index.create(Cc, Gc, pc, t=100, b=5)
+    log(f"ADC: data + coarse quantizer (K={K}) in {time.time() - t0:.1f}s")
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sample = torch.from_numpy(datagen.training_rows(5, N) if N > 1_000_000 else np.arange(N)).cuda()
+    out = {"metric": "Graph-D-ADC recall@{1,10,100} of the true nearest neighbour and ms/query vs L",
+           "unit": "ms/query", "workload": f"sift10m mixture: N={N} x {d} uint8, {nq} queries, K={K} coarse centers "
+                                            f"(data rows), coarse index P=2 x n=128, R=16",
+           "points": []}
+    for m in (8, 16):
+        t0 = time.time()
+        Rs = (X[sample].to(torch.float32) - Cf[assign[sample].long()]).contiguous()
+        cb = ann.ann_train_centers(Rs, m, 256, 10, datagen.kmeans_init_rows(5, Rs.shape[0], 256))
+        del Rs
+        codes = ann.ann_pq_encode(X, Cf, assign, cb)
+        torch.cuda.synchronize()
+        log(f"ADC m={m}: codebooks + codes in {time.time() - t0:.1f}s")
+        for L in (10_000, 30_000, 100_000):
+            w = min(128, max(8, int(2.5 * L * K / N)))   # lists enough to hold L candidates, with margin
+            Tc = max(256, 2 * w)
+
+            def step():
+                return ann.graph_d_adc_search(ixc, Q, w, Tc, offsets, members, Cf, codes, cb, L, 100,
+                                              stream=stream)
+
+            ids, keys, seen, _ = step()
+            torch.cuda.synchronize()
+            t = time_steps(torch, step, max(1, min(args.steps, 5)), 1, flush, stream)
+            ids = ids.long()
+            rec = {r: float((ids[:, :r] == gt[:, None]).any(1).float().mean().item()) for r in (1, 10, 100)}
+            pt = {"bytes_per_code": m, "L": L, "lists": w, "coarse_T": Tc, "recall@1": rec[1], "recall@10": rec[10],
+                  "recall@100": rec[100], "ms_per_query": statistics.mean(t) / nq,
+                  "mean_examined": float(seen.double().mean().item())}
+            log(f"ADC {pt}")
+            out["points"].append(pt)
     print(json.dumps(out), flush=True)
 
 

@@ -196,6 +196,20 @@ def ann_adc_rerank(queries, lists, offsets, members, centers, codes, codebooks, 
     return ids, keys, seen
 
 
+def graph_d_adc_search(coarse_index, queries, w, Tc, offsets, members, centers_f32, codes, codebooks, L, T,
+                       stream=None):
+    """Graph-D-ADC (Sec. 5.4) end to end: Algorithm 1 over the index of the
+    coarse centers (k = w lists, budget Tc) gives each query's lists, then
+    ann_adc_rerank ranks the first L members of those lists.  queries: device
+    tensor of the coarse index's dtype (uint8 queries are widened to float32
+    for the re-ranking).  Returns (ids, keys, examined, lists)."""
+    import torch
+    lists, _, _ = ann_search_batch(coarse_index, queries, w, Tc, kmax=w, stream=stream)
+    qf = queries if queries.dtype == torch.float32 else queries.to(torch.float32)
+    ids, keys, seen = ann_adc_rerank(qf, lists, offsets, members, centers_f32, codes, codebooks, L, T, stream)
+    return ids, keys, seen, lists
+
+
 def ann_train_centers(train, P, n, iters, init_rows: np.ndarray, want_f64=False, stream=None):
     import torch
     ntrain, d = train.shape

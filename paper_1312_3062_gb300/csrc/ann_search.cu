@@ -49,17 +49,19 @@ struct Tune {
     int bcap;
     bool stage;         // stage the next pop's neighbour vectors (cp.async)
     bool tickets = true;  // persistent form: pull queries from a ticket (else a fixed grid-stride share)
+    int spill_heap = (int)kSpillHeap;  // large budgets: queue entries kept in shared memory
 };
 
 // Warps per CTA: the count that keeps the most warps resident per SM given
 // the per-warp shared-memory slice (ties go to more warps per CTA).
-static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
+static Tune choose_tune_heap(const DevIndex &ix, int capT, int kmax, int spill_heap) {
     Tune t;
+    t.spill_heap = spill_heap;
     // bridge batch: budgets below the windowed kernels pop few bridges
     t.bcap = capT >= kWindowedFromT ? 128 : 64;
     t.stage = true;
     WarpLayout L = make_layout(ix.dtype, ix.d, ix.P, ix.n, ix.PA, capT, kmax, t.bcap, ix.b, ix.R, true,
-                               ix.ngroups > 0, capT >= kWindowedFromT);
+                               ix.ngroups > 0, capT >= kWindowedFromT, (uint32_t)t.spill_heap);
     const size_t per_sm = 228 * 1024, per_cta_reserved = 1024;
     size_t budget = g_smem_optin ? g_smem_optin : 227 * 1024;
     // register-file limit of the kernel (both instantiations use the same budget)
@@ -85,6 +87,10 @@ static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
     }
     t.warps = best_w;
     return t;
+}
+
+static Tune choose_tune(const DevIndex &ix, int capT, int kmax) {
+    return choose_tune_heap(ix, capT, kmax, (int)kSpillHeap);
 }
 
 
@@ -122,7 +128,7 @@ static int plan_launch(const SearchArgs &base, int capT, bool persistent, const 
     const Tune tn = tune ? *tune : choose_tune(A.ix, capT, A.kmax);
     A.bcap = tn.bcap;
     A.L = make_layout(A.ix.dtype, A.ix.d, A.ix.P, A.ix.n, A.ix.PA, capT, A.kmax, tn.bcap, A.ix.b, A.ix.R,
-                      tn.stage, A.ix.ngroups > 0, capT >= kWindowedFromT);
+                      tn.stage, A.ix.ngroups > 0, capT >= kWindowedFromT, (uint32_t)tn.spill_heap);
     A.list = list;
     A.list_count = list_count;
     A.list_len = list_len;
@@ -352,8 +358,11 @@ static int record_persistent(const PlanCache *pc, const SearchArgs &A, int64_t n
 }
 
 // Launch shapes worth measuring for a bucket: the analytic choice, fewer warps
-// per CTA (finer CTA granularity, fewer registers per SM in use), and the
-// analytic choice without cp.async staging.  All give identical results.
+// per CTA (finer CTA granularity, fewer registers per SM in use), the
+// analytic choice without cp.async staging, with fixed shares instead of the
+// ticket, and, for large budgets, other shared-memory heap capacities (a
+// smaller heap leaves room for more resident queries, a larger one moves
+// entries out less often).  All give identical results.
 static std::vector<Tune> tune_candidates(const DevIndex &ix, int capT, int kmax) {
     const Tune d = choose_tune(ix, capT, kmax);
     std::vector<Tune> c{d};
@@ -361,6 +370,15 @@ static std::vector<Tune> tune_candidates(const DevIndex &ix, int capT, int kmax)
         if (w < d.warps) c.push_back(Tune{w, d.bcap, true, true});
     c.push_back(Tune{d.warps, d.bcap, false, true});
     c.push_back(Tune{d.warps, d.bcap, true, false});  // the plain form's fixed grid-stride shares
+    if (capT >= kWindowedFromT)
+        for (int hc : {256, 1024, 2048})
+            if (hc < capT) {
+                Tune t = d;
+                t.spill_heap = hc;
+                Tune a = choose_tune_heap(ix, capT, kmax, hc);
+                t.warps = a.warps;
+                c.push_back(t);
+            }
     return c;
 }
 

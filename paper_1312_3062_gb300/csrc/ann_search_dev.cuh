@@ -53,16 +53,17 @@ struct WarpLayout {
 constexpr uint32_t kStageBytes = 4096;
 
 // Large-budget ("spilling") kernels keep at most this many queue entries in
-// shared memory; the rest of the queue and the visited set live in the
-// warp's global scratch, so a query's shared-memory slice does not grow with
-// the budget.
+// shared memory by default (the autotuner also tries other capacities); the
+// rest of the queue and the visited set live in the warp's global scratch,
+// so a query's shared-memory slice does not grow with the budget.
 constexpr uint32_t kSpillHeap = 512;
 
 __host__ __device__ inline uint32_t align_up(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n, int PA, int capT,
                                                   int kmax, int bcap, int b, int R, bool stage = true,
-                                                  bool grouped = false, bool spill = false) {
+                                                  bool grouped = false, bool spill = false,
+                                                  uint32_t spill_heap = kSpillHeap) {
     WarpLayout L;
     uint32_t o = 0;
     L.q = o;      o = align_up(o + (uint32_t)d * (dtype == ANN_U8 ? 1u : 4u), 16);
@@ -72,7 +73,7 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.sc = o;     o = align_up(o + (uint32_t)P * n, 16);  // center id at each rank, every part
     uint32_t lpn = 1;
     while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
-    const uint32_t qcap = spill && (uint32_t)capT > kSpillHeap ? kSpillHeap : (uint32_t)capT;
+    const uint32_t qcap = spill && (uint32_t)capT > spill_heap ? spill_heap : (uint32_t)capT;
     uint32_t hc = qcap > lpn ? qcap : lpn;
     L.heap_cap = hc;
     L.heap = o;   o = align_up(o + 8u * hc, 16);
@@ -777,45 +778,60 @@ __device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout 
         }
         __syncwarp();
         uint32_t np = 0;
-        for (uint32_t g = lane; g < run; g += 32) {
-            while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
-            const uint32_t jj = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
-            const uint32_t a = __ldg(ix.sleaf + jj);
-            const uint32_t c0 = PA == 1 ? a : (pow2n ? (a >> logn) : a / n);
-            const uint32_t c1 = PA == 1 ? 0u : a - c0 * n;
-            const uint32_t kA = PA == 1 ? D[c0] : KeyOps<DT>::add_lo(D[c0], D[n + c1]);
-            if (kA <= theta) continue;  // the first pass owns it
-            const uint32_t kb = nodes[4 * np + 2], sw = nodes[4 * np + 3], sfx = sw >> 16;
-            uint32_t key = KeyOps<DT>::add_lo(kA, kb);
-            if (key > hik) continue;
-            if (DT == ANN_F32) {
-                if (!first && KeyOps<DT>::add_hi(KeyOps<DT>::up(kA), KeyOps<DT>::up(kb)) < lok) continue;
-                uint32_t d0, d1, d2 = 0u, d3 = 0u;
-                d0 = D[c0];
-                if (PA == 1) {
-                    d1 = D[n + sfx];
-                } else {
-                    d1 = D[n + c1];
-                    if (nsuf == 1) {
-                        d2 = D[2 * n + sfx];
-                    } else {
-                        const uint32_t c2 = pow2n ? (sfx >> logn) : sfx / n;
-                        d2 = D[2 * n + c2];
-                        d3 = D[3 * n + (sfx - c2 * n)];
-                    }
+        constexpr int U2 = 2;  // leaf loads in flight per lane
+        for (uint32_t g0 = lane; g0 < run; g0 += 32 * U2) {
+            uint32_t jjv[U2], av[U2], npv[U2];
+#pragma unroll
+            for (int u = 0; u < U2; u++) {
+                const uint32_t g = g0 + 32 * u;
+                jjv[u] = 0xffffffffu;
+                if (g < run) {
+                    while (np + 1 < nl && nodes[4 * (np + 1) + 1] <= g) np++;
+                    npv[u] = np;
+                    jjv[u] = nodes[4 * np + 0] + (g - nodes[4 * np + 1]);
+                    av[u] = __ldg(ix.sleaf + jjv[u]);
                 }
-                key = KeyOps<DT>::sum4(d0, d1, d2, d3);
-                if (key > hik) continue;
             }
-            if (!first && key < lok) continue;
-            const uint32_t rpre = PA == 1 ? (uint32_t)rk[c0] : (((uint32_t)rk[c0] << 8) | rk[n + c1]);
-            const uint32_t ranks = (rpre << (8 * nsuf)) | (sw & 0xffffu);
-            const uint64_t comp = ((uint64_t)key << 32) | ranks;
-            if (comp <= hi && (first || comp > lo)) {
-                const uint32_t slot = atomicAdd(&cnt[0], 1u);
-                if (slot < ocap) {
-                    okey[slot] = comp;
-                    oval[slot] = __ldg(ix.sidx + jj);
+#pragma unroll
+            for (int u = 0; u < U2; u++) {
+                if (jjv[u] == 0xffffffffu) continue;
+                const uint32_t jj = jjv[u], a = av[u], nq = npv[u];
+                const uint32_t c0 = PA == 1 ? a : (pow2n ? (a >> logn) : a / n);
+                const uint32_t c1 = PA == 1 ? 0u : a - c0 * n;
+                const uint32_t kA = PA == 1 ? D[c0] : KeyOps<DT>::add_lo(D[c0], D[n + c1]);
+                if (kA <= theta) continue;  // the first pass owns it
+                const uint32_t kb = nodes[4 * nq + 2], sw = nodes[4 * nq + 3], sfx = sw >> 16;
+                uint32_t key = KeyOps<DT>::add_lo(kA, kb);
+                if (key > hik) continue;
+                if (DT == ANN_F32) {
+                    if (!first && KeyOps<DT>::add_hi(KeyOps<DT>::up(kA), KeyOps<DT>::up(kb)) < lok) continue;
+                    uint32_t d1, d2 = 0u, d3 = 0u;
+                    const uint32_t d0 = D[c0];
+                    if (PA == 1) {
+                        d1 = D[n + sfx];
+                    } else {
+                        d1 = D[n + c1];
+                        if (nsuf == 1) {
+                            d2 = D[2 * n + sfx];
+                        } else {
+                            const uint32_t c2 = pow2n ? (sfx >> logn) : sfx / n;
+                            d2 = D[2 * n + c2];
+                            d3 = D[3 * n + (sfx - c2 * n)];
+                        }
+                    }
+                    key = KeyOps<DT>::sum4(d0, d1, d2, d3);
+                    if (key > hik) continue;
+                }
+                if (!first && key < lok) continue;
+                const uint32_t rpre = PA == 1 ? (uint32_t)rk[c0] : (((uint32_t)rk[c0] << 8) | rk[n + c1]);
+                const uint32_t ranks = (rpre << (8 * nsuf)) | (sw & 0xffffu);
+                const uint64_t comp = ((uint64_t)key << 32) | ranks;
+                if (comp <= hi && (first || comp > lo)) {
+                    const uint32_t slot = atomicAdd(&cnt[0], 1u);
+                    if (slot < ocap) {
+                        okey[slot] = comp;
+                        oval[slot] = __ldg(ix.sidx + jj);
+                    }
                 }
             }
         }
@@ -856,16 +872,18 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     uint32_t *glist = (uint32_t *)(smem + L.glist);  // 5 words per group: start, count, kpre, D2, ranks
     const int nsuf = P - PA;
     if (lane == 0) cnt[0] = 0;
-    // Split walk (suffix-major copy present): the first pass lists the prefix
+    // Split walk (suffix-major copy present, and a single pass would list
+    // more than kSplitNodes prefix nodes): the first pass lists the prefix
     // nodes with bound A <= theta, the second (walk_suffix) the suffix nodes
     // with bound B <= bound2, so that A + B <= hi is covered by one of them;
     // theta splits the window's excess over the smallest possible A + B in
     // proportion to the parts on each side.  Otherwise one pass lists the
-    // prefix nodes with A + min B <= hi.
-    const bool split = !GRP && ix.sidx != nullptr;
+    // prefix nodes with A + min B <= hi (narrow windows: cheaper).
+    constexpr uint32_t kSplitNodes = 256;
+    const bool can_split = !GRP && ix.sidx != nullptr;
     uint32_t theta = 0, bound2 = 0;
     bool pass2 = false;
-    if (split) {
+    if (can_split) {
         const uint32_t minA = PA == 1 ? sk(0) : KeyOps<DT>::add_lo(sk(0), sk(n));
         if (DT == ANN_U8) {
             int64_t ex = (int64_t)hik - (int64_t)minA - (int64_t)msuf;
@@ -887,30 +905,43 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
             bound2 = pass2 ? __float_as_uint(b2) : 0u;
         }
     }
-    auto admitA = [&](uint32_t kA) -> bool {
-        return split ? kA <= theta : KeyOps<DT>::add_lo(kA, msuf) <= hik;
-    };
-    // candidate part-1 ranks per r0 (PA == 2), or 0/1 per r0 (PA == 1)
+    auto admit1 = [&](uint32_t kA) -> bool { return KeyOps<DT>::add_lo(kA, msuf) <= hik; };  // single pass
+    auto admit2 = [&](uint32_t kA) -> bool { return kA <= theta; };                          // split
+    // candidate part-1 ranks per r0 (PA == 2), or 0/1 per r0 (PA == 1), for
+    // the single pass (pref) and the split (kept in the node area meanwhile)
+    uint32_t *pref2 = nodes;
+    uint32_t single_total = 0;
     for (int r0 = lane; r0 < n; r0 += 32) {
-        uint32_t c;
+        uint32_t c1, c2 = 0;
         if (PA == 1) {
-            c = admitA(sk(r0)) ? 1u : 0u;
+            c1 = admit1(sk(r0)) ? 1u : 0u;
+            c2 = can_split && admit2(sk(r0)) ? 1u : 0u;
         } else {
-            uint32_t a0 = sk(r0);
-            if (!admitA(KeyOps<DT>::add_lo(a0, sk(n)))) {
-                c = 0;
-            } else {
+            const uint32_t a0 = sk(r0);
+            auto count = [&](bool two) -> uint32_t {
+                if (!(two ? admit2(KeyOps<DT>::add_lo(a0, sk(n))) : admit1(KeyOps<DT>::add_lo(a0, sk(n))))) return 0;
                 int lo1 = 1, hi1 = n;  // answer in [1, n]
                 while (lo1 < hi1) {
-                    int mid = (lo1 + hi1 + 1) >> 1;
-                    if (admitA(KeyOps<DT>::add_lo(a0, sk(n + mid - 1)))) lo1 = mid;
+                    const int mid = (lo1 + hi1 + 1) >> 1;
+                    const uint32_t kA = KeyOps<DT>::add_lo(a0, sk(n + mid - 1));
+                    if (two ? admit2(kA) : admit1(kA)) lo1 = mid;
                     else hi1 = mid - 1;
                 }
-                c = (uint32_t)lo1;
-            }
+                return (uint32_t)lo1;
+            };
+            c1 = count(false);
+            if (can_split) c2 = count(true);
         }
-        pref[r0] = c;
+        pref[r0] = c1;
+        if (can_split) pref2[r0] = c2;  // the node area holds >= 256 words when the copy exists (no group level)
+        single_total += c1;
     }
+    single_total = __reduce_add_sync(0xffffffffu, single_total);
+    const bool split = can_split && single_total > kSplitNodes;
+    if (!split) pass2 = false;
+    __syncwarp();
+    if (split)
+        for (int r0 = lane; r0 < n; r0 += 32) pref[r0] = pref2[r0];
     __syncwarp();
     warp_exclusive_scan(pref, n);
     const uint32_t total = pref[n];

@@ -112,6 +112,13 @@ def training_rows(workload: int, N: int, cap: int = 1_000_000) -> np.ndarray | N
     return np.sort(rng.choice(N, size=cap, replace=False)).astype(np.int64)
 
 
+def coarse_rows(workload: int, N: int, K: int) -> np.ndarray:
+    """K distinct data rows (sorted) serving as the coarse centers of the
+    Graph-D-ADC stand-in (seeded)."""
+    rng = np.random.Generator(np.random.PCG64(_seq(workload, 60)))
+    return np.sort(rng.choice(N, size=K, replace=False)).astype(np.int64)
+
+
 def per_query_params(workload: int, nq: int, seed_salt: int = 20):
     """Per-query (k, T) for the uneven-batch workloads (3: log-uniform T in
     [64, 8192]; 5: k in {1,10,100}, T in {128,512,2048})."""

@@ -135,6 +135,40 @@ def check_rerank(gi, gk, oi, ok, Q, assign, C, codes, cb):
     assert near <= max(1, len(Q) // 10)
 
 
+@pytest.mark.parametrize("m,ks,L,T", [(8, 64, 1500, 100), (16, 32, 10 ** 9, 10)])
+def test_graph_d_adc_end_to_end_matches_oracle(ann, m, ks, L, T):
+    # the whole Graph-D-ADC query on the GPU: Algorithm 1 over a GPU-built
+    # index of the coarse centers (seeded data rows), then re-ranking of the
+    # first L members of the w lists it returns, against the oracle's
+    # graph_d_adc_search on the same seeded inputs (codes from the oracle)
+    X = datagen.mixture(31, 30000, 128, 60, np.uint8)
+    rng = np.random.default_rng(32)
+    K, w, Tc = 200, 12, 150   # lists of ~150 members: L = 1500 cuts inside the w-th list
+    Cc = np.ascontiguousarray(X[np.sort(rng.choice(len(X), K, replace=False))])
+    assign = oracle.exact_knn(Cc, X, 1)[0][:, 0].astype(np.int32)
+    R = (X.astype(np.float64) - Cc[assign].astype(np.float64)).astype(np.float32)
+    cb = oracle.kmeans(R, m, ks, 3, rng.choice(len(X), ks, replace=False)).astype(np.float32)
+    codes = oracle.pq_encode(X, Cc, assign, cb)
+    offsets, members = oracle.ivf_lists(assign, K)
+    pc = oracle.round_centers(oracle.kmeans(Cc, 2, 16, 5, rng.permutation(K)[:16]), np.uint8)
+    Gc = oracle.knn_graph(Cc, 10)[0]
+    bgc = oracle.bridge_graph(Cc, pc, 100, 5)
+    Q = datagen.mixture(33, 64, 128, 60, np.uint8)
+    want_lists, _, _ = oracle.search(Cc, Gc, pc, bgc, Q, w, Tc)
+    wi, wk, wseen = oracle.graph_d_adc_search(Cc, Gc, pc, bgc, offsets, members, codes, cb, Q, w, Tc, L, T)
+    # the coarse index built on the GPU from the same centers
+    Gd, _ = ann.ann_build_knn_graph(cuda(Cc), 10)
+    ixc = ann.Index.create(cuda(Cc), Gd, cuda(pc), t=100, b=5)
+    gi, gk, gseen, glists = ann.graph_d_adc_search(ixc, cuda(Q), w, Tc, cuda(offsets), cuda(members),
+                                                   cuda(Cc.astype(np.float32)), cuda(codes), cuda(cb), L, T)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(glists.cpu().numpy(), want_lists)       # the coarse step is bit-exact
+    np.testing.assert_array_equal(gseen.cpu().numpy(), wseen)
+    check_rerank(gi.cpu().numpy(), gk.cpu().numpy().astype(np.float64), wi, wk, Q.astype(np.float32), assign,
+                 Cc.astype(np.float32), codes, cb)
+    ixc.free()
+
+
 def test_adc_argument_checks(ann):
     Q = torch.zeros((2, 16), dtype=torch.float32, device="cuda")
     lists = torch.zeros((2, 1), dtype=torch.int32, device="cuda")

@@ -292,7 +292,9 @@ def test_sift10m_served_mix_search(sift10m):
                                   for t, c in ((128, 5), (512, 5), (2048, 6))]))
     wi, wk = oracle_search_big(X, 16, C, Q[sel], k[sel], T[sel], 100, first_limits(X, Q[sel], T[sel]))
     np.testing.assert_array_equal(ids[sel], wi)
-    np.testing.assert_array_equal(keys[sel].astype(np.float64), wk)
+    got = keys[sel].astype(np.float64)
+    got[got == 0xFFFFFFFF] = np.inf        # padding: UINT32_MAX on the GPU, +inf in the oracle
+    np.testing.assert_array_equal(got, wk)
     # the same sampled queries submitted to the server, one request each
     import ctypes
     import time
@@ -315,7 +317,9 @@ def test_sift10m_served_mix_search(sift10m):
                 time.sleep(0.001)
             assert ss[0] == 0
             np.testing.assert_array_equal(si[0], wi[j, :kj])
-            np.testing.assert_array_equal(sk[0].view(np.uint32).astype(np.float64), wk[j, :kj])
+            sv = sk[0].view(np.uint32).astype(np.float64)
+            sv[sv == 0xFFFFFFFF] = np.inf
+            np.testing.assert_array_equal(sv, wk[j, :kj])
     finally:
         ann.lib.ann_server_destroy(srv)
 
