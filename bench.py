@@ -883,7 +883,12 @@ def run_adc(args, rank, ws, log, torch, ann, datagen):
     for m in (8, 16):
         t0 = time.time()
         Rs = (X[sample].to(torch.float32) - Cf[assign[sample].long()]).contiguous()
-        cb = ann.ann_train_centers(Rs, m, 256, 10, datagen.kmeans_init_rows(5, Rs.shape[0], 256))
+        # the per-part k-means takes at most 4 parts per call: train the m
+        # parts four at a time over their column slices
+        dp = d // m
+        init = datagen.kmeans_init_rows(5, Rs.shape[0], 256)
+        cb = torch.cat([ann.ann_train_centers(Rs[:, g * dp:(g + 4) * dp].contiguous(), 4, 256, 10, init)
+                        for g in range(0, m, 4)], 0).contiguous()
         del Rs
         codes = ann.ann_pq_encode(X, Cf, assign, cb)
         torch.cuda.synchronize()

@@ -46,6 +46,7 @@ struct WarpLayout {
     uint32_t q, tabD, rank, sk, sc, heap, hash, rbuf, bkey, bidx, pref, nodes, cand, ckey, wref, wkey, stage, misc,
         total;
     uint32_t heap_cap, hash_log, bcap, ncap, gcap, glist, stage_rows, stage_stride;
+    uint32_t sc_parts;  // parts whose centers are kept in rank order (all of them when split walks may run)
 };
 
 // Rows of the next pop's neighbours staged in shared memory: on when a whole
@@ -70,7 +71,11 @@ __host__ __device__ inline WarpLayout make_layout(int dtype, int d, int P, int n
     L.tabD = o;   o = align_up(o + 4u * P * n, 16);
     L.rank = o;   o = align_up(o + (uint32_t)P * n, 16);
     L.sk = 0;     // sorted keys are read as D[sc[r]]
-    L.sc = o;     o = align_up(o + (uint32_t)P * n, 16);  // center id at each rank, every part
+    // center id at each rank: the prefix parts, and with the large-budget
+    // layout every part (the suffix pass of a split walk reads them); below
+    // it the extra bytes would cost a resident query per SM
+    L.sc_parts = spill ? (uint32_t)P : (uint32_t)PA;
+    L.sc = o;     o = align_up(o + L.sc_parts * n, 16);
     uint32_t lpn = 1;
     while (lpn < (uint32_t)n) lpn <<= 1;  // the per-part sort borrows the heap region
     const uint32_t qcap = spill && (uint32_t)capT > spill_heap ? spill_heap : (uint32_t)capT;
@@ -654,6 +659,40 @@ struct WalkState {
     int gbuf;             // which of the two scratch buffers holds it
 };
 
+// A walk's output buffer is about to overflow: lower the window end hi to the
+// median of 32 entries sampled from the buffer, keep the entries at or below
+// it and let the walk go on with the lower end.  Entries are distinct
+// (key, ranks) composites, so at least 16 leave the buffer, and the buffer
+// ends up holding every bridge of (lo, final hi] -- no second walk needed.
+__device__ inline void walk_trim(uint64_t *okey, uint32_t *oval, uint32_t *cnt, uint64_t &hi, uint32_t &hik) {
+    const int lane = lane_id();
+    const unsigned lt = (1u << lane) - 1;
+    const uint32_t c = cnt[0];  // >= 32
+    uint64_t smp[1] = {okey[(uint32_t)(((uint64_t)lane * c) >> 5)]};
+    reg_bitonic_sort_t<1, uint64_t>(smp);
+    const uint64_t t = __shfl_sync(0xffffffffu, smp[0], 15);
+    uint32_t w = 0;
+    for (uint32_t base = 0; base < c; base += 32) {
+        const uint32_t i = base + lane;
+        const bool valid = i < c;
+        const uint64_t k = valid ? okey[i] : 0ull;
+        const uint32_t v = valid ? oval[i] : 0u;
+        const bool keep = valid && k <= t;
+        const unsigned mk = __ballot_sync(0xffffffffu, keep);
+        __syncwarp();
+        if (keep) {  // in place: never past what this step read
+            okey[w + __popc(mk & lt)] = k;
+            oval[w + __popc(mk & lt)] = v;
+        }
+        w += __popc(mk);
+        __syncwarp();
+    }
+    if (lane == 0) cnt[0] = w;
+    hi = t;
+    hik = (uint32_t)(t >> 32);
+    __syncwarp();
+}
+
 // exclusive prefix sum over pref[0 .. n) in place, total in pref[n]
 __device__ __forceinline__ void warp_exclusive_scan(uint32_t *pref, int n) {
     const int lane = lane_id();
@@ -690,7 +729,7 @@ __device__ __forceinline__ void warp_exclusive_scan(uint32_t *pref, int n) {
 // exceeds theta -- each bridge is read by exactly one pass that can emit it.
 template <int DT>
 __device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
-                            uint64_t hi, uint32_t theta, uint32_t bound2, uint64_t *okey, uint32_t *oval,
+                            uint64_t &hi, uint32_t theta, uint32_t bound2, uint64_t *okey, uint32_t *oval,
                             uint32_t ocap, int64_t &nodes_here, int64_t &leaves_here) {
     const int lane = lane_id();
     const int n = ix.n, P = ix.P, PA = ix.PA, q0 = ix.PA, nsuf = P - PA;
@@ -701,7 +740,8 @@ __device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout 
     uint32_t *pref = (uint32_t *)(smem + L.pref);
     uint32_t *nodes = (uint32_t *)(smem + L.nodes);  // 4 words per node: start, count, key bound, (s << 16) | ranks
     uint32_t *cnt = (uint32_t *)(smem + L.misc);
-    const uint32_t hik = (uint32_t)(hi >> 32), lok = (uint32_t)(lo >> 32);
+    uint32_t hik = (uint32_t)(hi >> 32);
+    const uint32_t lok = (uint32_t)(lo >> 32);
     const bool pow2n = (n & (n - 1)) == 0;
     const int logn = 31 - __clz(n);
     // candidate ranks of the second suffix part per rank of the first
@@ -779,7 +819,10 @@ __device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout 
         __syncwarp();
         uint32_t np = 0;
         constexpr int U2 = 2;  // leaf loads in flight per lane
-        for (uint32_t g0 = lane; g0 < run; g0 += 32 * U2) {
+        for (uint32_t b0 = 0; b0 < run; b0 += 32 * U2) {
+            __syncwarp();
+            while (cnt[0] + 32u * U2 > ocap) walk_trim(okey, oval, cnt, hi, hik);
+            const uint32_t g0 = b0 + lane;
             uint32_t jjv[U2], av[U2], npv[U2];
 #pragma unroll
             for (int u = 0; u < U2; u++) {
@@ -851,7 +894,7 @@ __device__ void walk_suffix(const DevIndex &ix, uint8_t *smem, const WarpLayout 
 // bound D0 + D1 + D2[c2] + min D3 fits the window, and (2) reads their leaves.
 template <int DT, int UL, bool GRP>
 __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, uint64_t lo, bool first,
-                         uint64_t hi, uint64_t *okey, uint32_t *oval,
+                         uint64_t &hi, uint64_t *okey, uint32_t *oval,
                          uint32_t ocap) {
     const int lane = lane_id();
     const int n = ix.n, P = ix.P, PA = ix.PA;
@@ -864,7 +907,7 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     uint64_t *bkey = (uint64_t *)(smem + L.bkey);
     uint32_t *bidx = (uint32_t *)(smem + L.bidx);
     uint32_t *cnt = (uint32_t *)(smem + L.misc);
-    const uint32_t hik = (uint32_t)(hi >> 32);
+    uint32_t hik = (uint32_t)(hi >> 32);  // lowered, with hi, when the output buffer fills
     const bool pow2n = (n & (n - 1)) == 0;
     const int logn = 31 - __clz(n);
     const uint32_t msuf = cnt[3];     // min-suffix key sum, stored by the caller
@@ -880,7 +923,7 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
     // proportion to the parts on each side.  Otherwise one pass lists the
     // prefix nodes with A + min B <= hi (narrow windows: cheaper).
     constexpr uint32_t kSplitNodes = 256;
-    const bool can_split = !GRP && ix.sidx != nullptr;
+    const bool can_split = !GRP && ix.sidx != nullptr && L.sc_parts == (uint32_t)P;
     uint32_t theta = 0, bound2 = 0;
     bool pass2 = false;
     if (can_split) {
@@ -1044,7 +1087,11 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                         __syncwarp();
                         // (2) the leaves (c3) of the listed groups
                         uint32_t gp = 0;
-                        for (uint32_t e = lane; e < grun; e += 32) {
+                        for (uint32_t e0 = 0; e0 < grun; e0 += 32) {
+                            __syncwarp();
+                            while (cnt[0] + 32u > ocap) walk_trim(okey, oval, cnt, hi, hik);
+                            const uint32_t e = e0 + lane;
+                            if (e >= grun) continue;
                             while (gp + 1 < nlg && glist[5 * (gp + 1) + 1] <= e) gp++;
                             const uint32_t j = glist[5 * gp + 0] + (e - glist[5 * gp + 1]);
                             const uint32_t lf = __ldg(ix.leaf + j);
@@ -1082,7 +1129,10 @@ __device__ uint32_t walk(const DevIndex &ix, uint8_t *smem, const WarpLayout &L,
                 continue;
             }
             // UL leaves per lane per step, their loads in flight together
-            for (uint32_t g0 = lane; g0 < lt; g0 += 32 * UL) {
+            for (uint32_t b0 = 0; b0 < lt; b0 += 32 * UL) {
+                __syncwarp();
+                while (cnt[0] + 32u * UL > ocap) walk_trim(okey, oval, cnt, hi, hik);
+                const uint32_t g0 = b0 + lane;
                 uint32_t jv[UL], lfv[UL], npv[UL];
 #pragma unroll
                 for (int u = 0; u < UL; u++) {
@@ -1166,6 +1216,14 @@ __device__ __forceinline__ uint64_t window_end(uint64_t lo, bool first, uint32_t
     return (e << 32) | 0xffffffffull;
 }
 
+// The walk lowered the window end to fit its buffer: the next windows start
+// at the width that window ended up with.
+__device__ __forceinline__ void window_resize(WalkState &ws, uint64_t hi) {
+    const uint32_t base = ws.first ? ws.kmin : (uint32_t)(ws.lo >> 32);
+    const uint32_t w = (uint32_t)(hi >> 32) - base;
+    ws.width = w > 1 ? w : 1;
+}
+
 // Refill the batch: bridges after ws.lo in order.  Returns count (0 = none left).
 template <int DT, bool GRP>
 __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &L, WalkState &ws,
@@ -1175,7 +1233,9 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
     const int lane = lane_id();
     while (!ws.exhausted) {
         uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
+        const uint64_t hi0 = hi;
         uint32_t c = walk<DT, 1, GRP>(ix, smem, L, ws.lo, ws.first, hi, bkey, bidx, L.bcap);
+        if (hi != hi0) window_resize(ws, hi);
         if (c > L.bcap) {
             // too many in the window: halve it (in composite space)
             uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
@@ -1306,7 +1366,9 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
         ws.gpos = ws.gcnt = 0;
         while (!ws.exhausted) {
             uint64_t hi = window_end(ws.lo, ws.first, ws.kmin, ws.width, ws.kmaxall);
+            const uint64_t hi0 = hi;
             uint32_t c = walk<DT, 4, GRP>(ix, smem, L, ws.lo, ws.first, hi, gk0, gv0, gcap);
+            if (hi != hi0) window_resize(ws, hi);
                 if (c > gcap) {
                 // too many in the window: halve it (in composite space)
                 uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
@@ -1372,6 +1434,7 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
 template <int EPL, bool PACK>
 __device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_t *sc, int p, int n, int PA,
                                           uint32_t *first_keys, uint32_t *last_keys) {
+    // PA here: how many leading parts keep their centers in rank order
     const int lane = lane_id();
     using K = typename std::conditional<PACK, uint32_t, uint64_t>::type;
     constexpr int SH = PACK ? 8 : 32;
@@ -1388,7 +1451,7 @@ __device__ __forceinline__ void sort_part(const uint32_t *D, uint8_t *rk, uint8_
         if (r < n) {
             const uint32_t c = (uint32_t)(v[s] & (PACK ? 0xffu : 0xffffffffu));
             rk[p * n + c] = (uint8_t)r;
-            sc[p * n + r] = (uint8_t)c;
+            if (p < PA) sc[p * n + r] = (uint8_t)c;
         }
     }
     first_keys[p] = (uint32_t)(__shfl_sync(0xffffffffu, v[0], 0) >> SH);
@@ -1483,7 +1546,7 @@ __device__ void search_one(const SearchArgs &A, uint8_t *smem, int64_t qi, uint8
     uint32_t kmin = 0, kmaxall = 0;
     {
         uint32_t first_keys[kMaxP], last_keys[kMaxP];
-        sort_parts<DT>(D, rk, sc, P, n, PA, dp, first_keys, last_keys);
+        sort_parts<DT>(D, rk, sc, P, n, (int)L.sc_parts, dp, first_keys, last_keys);
         __syncwarp();
         // smallest / largest bridge keys (exact sums) and a lower bound of the
         // smallest suffix sum
