@@ -256,6 +256,8 @@ def bridge_graph_near(X: np.ndarray, centers: np.ndarray, t: int, b: int, querie
 def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, queries: np.ndarray,
            k, T, kmax: int | None = None, nthreads: int = 1, trace: bool = False, bridge_key_limit=None):
     """Algorithm 1 for each query.  k, T: scalars or per-query arrays.
+    nthreads: threads (0 = all cores); one query per thread, and threads left
+    over share each query's on-demand kNN row scans.
     graph: (N, R) int32 rows, or an int R to compute each popped row on demand
     (its R nearest other references by linear scan).
 
@@ -298,7 +300,7 @@ def search(X: np.ndarray, graph: np.ndarray, centers: np.ndarray, bg: dict, quer
                            _ptr(centers), len(bridges), _ptr(bridges), _ptr(offs), _ptr(refs),
                            _ptr(queries), nq, _ptr(k), _ptr(T), kmax, _ptr(ids), _ptr(keys),
                            _ptr(st), _ptr(disc) if trace else None, cap, None if lim is None else _ptr(lim),
-                           nthreads)
+                           _threads(nthreads))
     if rc != 0:
         raise ValueError("oracle_search: bad arguments")
     out = {name: st[:, i] for i, name in enumerate(STAT_NAMES)}

@@ -990,7 +990,52 @@ typedef struct {
     const uint64_t *bridges;
     const int64_t *boff;
     const int32_t *brefs;
+    int row_threads; /* threads that share one on-demand kNN row scan */
 } index_t;
+
+/* The R nearest other references of reference p by linear scan (Sec. 3.1:
+   Adj[p] of the neighbourhood graph), ascending (key, id).  The scan over
+   [0, N) is split into row_threads contiguous chunks; each chunk keeps its
+   own R smallest, and the chunks' lists are merged by the same insertion,
+   which gives the R smallest overall. */
+typedef struct {
+    const index_t *ix;
+    int64_t p, lo, hi;
+    double keys[64];
+    int64_t ids[64];
+    int len;
+} rowscan_t;
+
+static void *rowscan_worker(void *arg) {
+    rowscan_t *c = (rowscan_t *)arg;
+    const index_t *ix = c->ix;
+    const void *xp = row_ptr(ix->X, c->p, ix->d, ix->dtype);
+    c->len = 0;
+    for (int64_t j = c->lo; j < c->hi; j++) {
+        if (j == c->p) continue;
+        double kj = sqdist(xp, row_ptr(ix->X, j, ix->d, ix->dtype), ix->d, ix->dtype);
+        topk_insert(c->keys, c->ids, &c->len, ix->R, kj, j);
+    }
+    return NULL;
+}
+
+static void knn_row_scan(const index_t *ix, int64_t p, double *keys, int64_t *ids, int *len) {
+    int nt = ix->row_threads < 1 ? 1 : (ix->row_threads > 16 ? 16 : ix->row_threads);
+    rowscan_t c[16];
+    pthread_t th[16];
+    for (int t = 0; t < nt; t++) {
+        c[t].ix = ix;
+        c[t].p = p;
+        c[t].lo = ix->N * t / nt;
+        c[t].hi = ix->N * (t + 1) / nt;
+        if (t > 0) pthread_create(&th[t], NULL, rowscan_worker, &c[t]);
+    }
+    rowscan_worker(&c[0]);
+    for (int t = 1; t < nt; t++) pthread_join(th[t], NULL);
+    *len = 0;
+    for (int t = 0; t < nt; t++)
+        for (int i = 0; i < c[t].len; i++) topk_insert(keys, ids, len, ix->R, c[t].keys[i], c[t].ids[i]);
+}
 
 /* Bridge id -> its reference list (binary search over the sorted ids). */
 static int64_t bridge_lookup(const index_t *ix, uint64_t id, int64_t *len) {
@@ -1047,12 +1092,7 @@ static void search_one(const index_t *ix, const void *q, int k, int T, int kmax,
                 /* no stored graph: Adj[p] by its definition, the R nearest
                    other references by linear scan (Sec. 3.1) */
                 int len = 0;
-                for (int64_t j = 0; j < ix->N; j++) {
-                    if (j == p.id) continue;
-                    double kj = sqdist(row_ptr(ix->X, p.id, ix->d, ix->dtype), row_ptr(ix->X, j, ix->d, ix->dtype),
-                                       ix->d, ix->dtype);
-                    topk_insert(rowk, rowi, &len, ix->R, kj, j);
-                }
+                knn_row_scan(ix, p.id, rowk, rowi, &len);
                 for (int r = 0; r < ix->R; r++) rowbuf[r] = r < len ? (int32_t)rowi[r] : -1;
                 adj = rowbuf;
             }
@@ -1158,7 +1198,10 @@ int oracle_search(const void *X, int64_t N, int d, int dtype, const int32_t *gra
                   double *out_keys, int64_t *stats, int32_t *disc, int disc_cap, const double *bkey_limit,
                   int nthreads) {
     if (P > MAXP || P < 1 || d % P != 0 || R > 64) return -1;
-    index_t ix = {X, N, d, dtype, graph, R, P, n, centers, M, bridges, boff, brefs};
+    /* threads left over when there are fewer queries than threads share the
+       on-demand kNN row scans of each query */
+    int row_threads = nq > 0 && nthreads > nq ? (int)(nthreads / nq) : 1;
+    index_t ix = {X, N, d, dtype, graph, R, P, n, centers, M, bridges, boff, brefs, row_threads};
     job_t job = {&ix, queries, nq, k, T, kmax, out_ids, out_keys, stats, disc, disc_cap, bkey_limit, 0,
                  PTHREAD_MUTEX_INITIALIZER};
     if (nthreads <= 1) {

@@ -67,7 +67,7 @@ def test_sampled_search(sift1m, T, sel):
     bg = sift1m_bg[0] if sift1m_bg[0] is not None else oracle.bridge_graph(X, C, 100, 5)
     sift1m_bg[0] = bg
     Q = np.ascontiguousarray(Qall[sel])
-    wi, wk, wst = oracle.search(X, 20, C, bg, Q, 10, T, kmax=10, nthreads=len(sel))
+    wi, wk, wst = oracle.search(X, 20, C, bg, Q, 10, T, kmax=10, nthreads=0)
     gi, gk, gs = ann.ann_search_batch(ix, torch.from_numpy(Q).cuda(), 10, T, kmax=10)
     torch.cuda.synchronize()
     assert np.all(gs.cpu().numpy() == 0)
@@ -136,7 +136,7 @@ def test_gist1m_sampled_uneven_search(gist1m):
     bg = gist1m_bg[0] if gist1m_bg[0] is not None else oracle.bridge_graph(X, C, 100, 5)
     small = np.where(T <= 256)[0]
     sel = np.random.default_rng(33).choice(small, 8, replace=False)
-    wi, wk, _ = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=len(sel))
+    wi, wk, _ = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=0)
     np.testing.assert_array_equal(ids[sel], wi)
     fin = np.isfinite(wk)
     got = keys[sel].view(np.float32).astype(np.float64)
@@ -153,7 +153,7 @@ def test_gist1m_sampled_large_budget_search(gist1m):
     rng = np.random.default_rng(34)
     sel = np.sort(np.concatenate([rng.choice(np.flatnonzero(T >= 4096), 6, replace=False),
                                   rng.choice(np.flatnonzero((T >= 1024) & (T < 4096)), 2, replace=False)]))
-    wi, wk, wst = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=len(sel))
+    wi, wk, wst = oracle.search(X, 20, C, bg, Q[sel], k[sel], T[sel], kmax=100, nthreads=0)
     assert (wst["bridge_pops"] > 100).sum() >= 4     # the storm regime is exercised
     np.testing.assert_array_equal(ids[sel], wi)
     fin = np.isfinite(wk)
@@ -231,7 +231,7 @@ def oracle_search_big(X, R, C, Q, k, T, kmax, limits):
     for _ in range(10):
         todo = np.flatnonzero(~done)
         bg = oracle.bridge_graph_near(X, C, 100, 5, Q[todo], limits[todo])
-        wi, wk, st = oracle.search(X, R, C, bg, Q[todo], k[todo], T[todo], kmax=kmax, nthreads=len(todo),
+        wi, wk, st = oracle.search(X, R, C, bg, Q[todo], k[todo], T[todo], kmax=kmax, nthreads=0,
                                    bridge_key_limit=limits[todo])
         ok = st["over_limit"] == 0
         ids[todo[ok]], keys[todo[ok]] = wi[ok], wk[ok]
@@ -332,17 +332,24 @@ def test_hog4m_sampled_knn_rows_and_bridge_lists(hog4m):
 
 def test_hog4m_sampled_search(hog4m):
     # 20,000 queries at T in {256, 1024, 4096}, k = 10; 16 sampled queries
-    # against the oracle: identical ids, keys within 1e-5 relative
+    # (8 / 6 / 2) against the oracle in one pass with per-query budgets:
+    # identical ids, keys within 1e-5 relative
     ann, X, C, G, ix = hog4m
     Q = datagen.queries(4)
     rng = np.random.default_rng(404)
+    sel_all, T_all, ids_all, keys_all = [], [], [], []
     for T, c in ((256, 8), (1024, 6), (4096, 2)):
         ids, keys, st = ann.ann_search_batch(ix, torch.from_numpy(Q).cuda(), 10, T, kmax=10, mode=1)
         torch.cuda.synchronize()
         assert np.all(st.cpu().numpy() == 0)
         sel = np.sort(rng.choice(len(Q), c, replace=False))
-        wi, wk = oracle_search_big(X, 16, C, Q[sel], 10, T, 10, first_limits(X, Q[sel], T))
-        np.testing.assert_array_equal(ids.cpu().numpy()[sel], wi)
-        got = keys.cpu().numpy()[sel].astype(np.float64)
-        fin = np.isfinite(wk)
-        np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)
+        sel_all.append(sel)
+        T_all.append(np.full(c, T, np.int32))
+        ids_all.append(ids.cpu().numpy()[sel])
+        keys_all.append(keys.cpu().numpy()[sel])
+    sel, T, ids, keys = (np.concatenate(v) for v in (sel_all, T_all, ids_all, keys_all))
+    wi, wk = oracle_search_big(X, 16, C, Q[sel], 10, T, 10, first_limits(X, Q[sel], T))
+    np.testing.assert_array_equal(ids, wi)
+    got = keys.astype(np.float64)
+    fin = np.isfinite(wk)
+    np.testing.assert_allclose(got[fin], wk[fin], rtol=F32_RTOL, atol=0)

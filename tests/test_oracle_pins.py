@@ -516,6 +516,18 @@ def test_on_demand_rows_equal_stored_graph(oracle_lib):
     b = oracle.search(X, 7, C, bg, Qs, 5, 120, trace=True)
     np.testing.assert_array_equal(a[0], b[0])
     np.testing.assert_array_equal(a[2]["trace"], b[2]["trace"])
+    # spare threads split each row's scan (6 queries, 16 threads: 2 per row)
+    c = oracle.search(X, 7, C, bg, Qs, 5, 120, trace=True, nthreads=16)
+    np.testing.assert_array_equal(a[0], c[0])
+    np.testing.assert_array_equal(a[2]["trace"], c[2]["trace"])
+    # ties across chunk boundaries: duplicated rows
+    Xd = np.concatenate([X, X[:40]])
+    Gd, _ = oracle.knn_graph(Xd, 7)
+    bgd = oracle.bridge_graph(Xd, C, 10, 3)
+    d1 = oracle.search(Xd, Gd, C, bgd, Qs, 5, 150, trace=True)
+    d2 = oracle.search(Xd, 7, C, bgd, Qs[:2], 5, 150, trace=True, nthreads=16)
+    np.testing.assert_array_equal(d1[0][:2], d2[0])
+    np.testing.assert_array_equal(d1[2]["trace"][:2], d2[2]["trace"])
 
 
 @pytest.mark.parametrize("dtype", [np.uint8, np.float32])
