@@ -1237,7 +1237,9 @@ __device__ uint32_t refill(const DevIndex &ix, uint8_t *smem, const WarpLayout &
         uint32_t c = walk<DT, 1, GRP>(ix, smem, L, ws.lo, ws.first, hi, bkey, bidx, L.bcap);
         if (hi != hi0) window_resize(ws, hi);
         if (c > L.bcap) {
-            // too many in the window: halve it (in composite space)
+            // too many in the window: halve it (in composite space).  A walk
+            // lowers its own end before its buffer overflows, so this is a
+            // guard only
             uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
             uint64_t span = hi - base;
             if (span == 0) { cap_err = true; return 0; }
@@ -1369,8 +1371,10 @@ __device__ uint32_t refill_windowed(const DevIndex &ix, uint8_t *smem, const War
             const uint64_t hi0 = hi;
             uint32_t c = walk<DT, 4, GRP>(ix, smem, L, ws.lo, ws.first, hi, gk0, gv0, gcap);
             if (hi != hi0) window_resize(ws, hi);
-                if (c > gcap) {
-                // too many in the window: halve it (in composite space)
+            if (c > gcap) {
+                // too many in the window: halve it (in composite space).  A
+                // walk lowers its own end before its buffer overflows, so this
+                // is a guard only
                 uint64_t base = ws.first ? ((uint64_t)ws.kmin << 32) : ws.lo + 1;
                 uint64_t span = hi - base;
                 if (span == 0) { cap_err = true; return 0; }
