@@ -245,15 +245,33 @@ def sweep_t90(args, torch, ann, W, log):
         torch.cuda.synchronize()
         r = recall_at_10(torch, ids, W)
         return args.T, r, [(args.T, r)]
-    table = []
-    for T in T_GRID:
-        ids, _, st = ann.ann_search_batch(W["index"], W["Q"], K, T, kmax=K, mode=1)
+
+    def rec(T):
+        ids, _, _ = ann.ann_search_batch(W["index"], W["Q"], K, T, kmax=K, mode=1)
         torch.cuda.synchronize()
         r = recall_at_10(torch, ids, W)
         table.append((T, r))
         log(f"T={T} recall@10={r:.4f}")
+        return r
+
+    # the sqrt(2) grid brackets the smallest budget with recall@10 >= 0.9;
+    # bisection on the integers then narrows the bracket to 1/64 of the
+    # budget (the budget returned always has recall >= 0.9)
+    table = []
+    prev = None
+    for T in T_GRID:
+        r = rec(T)
         if r >= 0.9:
-            return T, r, table
+            lo, hi, rhi = prev, T, r
+            while lo is not None and hi - lo > max(1, hi // 64):
+                mid = (lo + hi) // 2
+                rm = rec(mid)
+                if rm >= 0.9:
+                    hi, rhi = mid, rm
+                else:
+                    lo = mid
+            return hi, rhi, sorted(table)
+        prev = T
     return T_GRID[-1], table[-1][1], table
 
 
