@@ -8,8 +8,9 @@ Headline workload (default): the served SIFT-shaped index, N = 10,000,000 x
 HBM; 10,000 queries from the same mixture; exact kNN graph R = 16 (GPU,
 tensor cores), P = 4 x n = 256 part dictionaries (GPU k-means, 10
 iterations on a seeded 1M-row sample), bridge graph t = 100, b <= 5 (GPU).
-T90 = the smallest budget on the grid {64, 90, 128, 181, 256, ...} (steps of
-sqrt 2) with mean recall@10 >= 0.9; every timed step searches all 10,000
+T90 = the smallest budget with mean recall@10 >= 0.9: the grid {64, 90, 128,
+181, 256, ...} (steps of sqrt 2) brackets it and bisection on the integers
+narrows the bracket to 1/64 of the budget; every timed step searches all 10,000
 queries at T90, k = 10.  The served form replays Poisson arrivals of 1-512
 query requests at T90 and, separately, the workload's own request mix (k in
 {1, 10, 100}, T in {128, 512, 2048}) against the plain form on that mix.
