@@ -903,9 +903,20 @@ extern "C" int ann_index_load(const char *path, int device, ann_index **out) {
     }
     void *dX = nullptr, *dC = nullptr;
     int32_t *dG = nullptr;
-    ANN_CUDA(cudaMalloc(&dX, X.size()));
-    ANN_CUDA(cudaMalloc((void **)&dG, 4 * G.size()));
-    ANN_CUDA(cudaMalloc(&dC, C.size()));
+    // staging copies on the device, freed on every return (the index copies them)
+    struct Staged {
+        void *p[3] = {};
+        ~Staged() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } staged;
+    ANN_CUDA(cudaMalloc(&staged.p[0], X.size()));
+    ANN_CUDA(cudaMalloc(&staged.p[1], 4 * G.size()));
+    ANN_CUDA(cudaMalloc(&staged.p[2], C.size()));
+    dX = staged.p[0];
+    dG = (int32_t *)staged.p[1];
+    dC = staged.p[2];
     ANN_CUDA(cudaMemcpy(dX, X.data(), X.size(), cudaMemcpyHostToDevice));
     ANN_CUDA(cudaMemcpy(dG, G.data(), 4 * G.size(), cudaMemcpyHostToDevice));
     ANN_CUDA(cudaMemcpy(dC, C.data(), C.size(), cudaMemcpyHostToDevice));
@@ -926,9 +937,5 @@ extern "C" int ann_index_load(const char *path, int device, ann_index **out) {
     d.bridge_ids = ids.data();
     d.bridge_offsets = offs.data();
     d.bridge_refs = flat.data();
-    int r = ann_index_create(&d, out);
-    cudaFree(dX);
-    cudaFree(dG);
-    cudaFree(dC);
-    return r;
+    return ann_index_create(&d, out);
 }

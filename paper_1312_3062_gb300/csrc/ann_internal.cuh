@@ -17,6 +17,36 @@ void set_error(const std::string &msg);
 int fail(int code, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+// Stream-ordered device buffers (cudaMallocAsync) released by cudaFreeAsync
+// on the same stream when the owner goes out of scope, so that an early
+// error return frees whatever was already taken.
+class AsyncBufs {
+  public:
+    explicit AsyncBufs(cudaStream_t s) : s_(s) {}
+    AsyncBufs(const AsyncBufs &) = delete;
+    AsyncBufs &operator=(const AsyncBufs &) = delete;
+    ~AsyncBufs() {
+        for (int i = n_ - 1; i >= 0; i--) cudaFreeAsync(p_[i], s_);
+    }
+    template <class T>
+    cudaError_t alloc(T **out, size_t bytes) {
+        if (n_ == kMax) return cudaErrorMemoryAllocation;
+        void *q = nullptr;
+        const cudaError_t e = cudaMallocAsync(&q, bytes, s_);
+        if (e == cudaSuccess) {
+            p_[n_++] = q;
+            *out = (T *)q;
+        }
+        return e;
+    }
+
+  private:
+    static constexpr int kMax = 16;
+    cudaStream_t s_;
+    void *p_[kMax] = {};
+    int n_ = 0;
+};
+
 #define ANN_CUDA(call)                                                   \
     do {                                                                 \
         cudaError_t _e = (call);                                         \

@@ -242,13 +242,14 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
         return knn_f32_tensor((const float *)refs, N, (const float *)queries, nq, d, k, exclude_self, out_ids,
                               (uint32_t *)out_keys, s);
     uint32_t *rn = nullptr, *qn = nullptr;
+    AsyncBufs bufs(s);  // released on return
     if (dtype == ANN_U8) {
-        ANN_CUDA(cudaMallocAsync((void **)&rn, 4 * N, s));
+        ANN_CUDA(bufs.alloc(&rn, 4 * N));
         norms_u8_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>((const uint8_t *)refs, N, d, rn);
         if (queries == refs && nq <= N) {  // the query rows are the first nq reference rows
             qn = rn;
         } else {
-            ANN_CUDA(cudaMallocAsync((void **)&qn, 4 * nq, s));
+            ANN_CUDA(bufs.alloc(&qn, 4 * nq));
             norms_u8_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>((const uint8_t *)queries, nq, d, qn);
         }
     }
@@ -266,8 +267,6 @@ extern "C" int ann_exact_knn(const void *refs, int64_t N, const void *queries, i
                                                            (uint32_t *)out_keys);
     }
     ANN_CUDA(cudaGetLastError());
-    if (rn) ANN_CUDA(cudaFreeAsync(rn, s));
-    if (qn && qn != rn) ANN_CUDA(cudaFreeAsync(qn, s));
     return ANN_OK;
 }
 

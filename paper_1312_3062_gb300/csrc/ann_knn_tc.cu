@@ -474,10 +474,11 @@ int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_
     uint32_t *rn = nullptr, *qn = nullptr;
     int *derr = nullptr;
     uint64_t *hl = nullptr;
-    ANN_CUDA(cudaMallocAsync((void **)&hl, (size_t)nq * 2 * k * 8, s));
-    ANN_CUDA(cudaMallocAsync((void **)&rb, (size_t)N * d * 2, s));
-    ANN_CUDA(cudaMallocAsync((void **)&rn, (size_t)N * 4, s));
-    ANN_CUDA(cudaMallocAsync((void **)&derr, sizeof(int), s));
+    AsyncBufs bufs(s);  // every buffer below is released on return
+    ANN_CUDA(bufs.alloc(&hl, (size_t)nq * 2 * k * 8));
+    ANN_CUDA(bufs.alloc(&rb, (size_t)N * d * 2));
+    ANN_CUDA(bufs.alloc(&rn, (size_t)N * 4));
+    ANN_CUDA(bufs.alloc(&derr, sizeof(int)));
     ANN_CUDA(cudaMemsetAsync(derr, 0, sizeof(int), s));
     to_bf16_kernel<<<(unsigned)((N * d + 255) / 256), 256, 0, s>>>(refs, N * d, rb);
     norms_kernel<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(refs, N, d, rn);
@@ -485,8 +486,8 @@ int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_
         qb = rb;
         qn = rn;
     } else {
-        ANN_CUDA(cudaMallocAsync((void **)&qb, (size_t)nq * d * 2, s));
-        ANN_CUDA(cudaMallocAsync((void **)&qn, (size_t)nq * 4, s));
+        ANN_CUDA(bufs.alloc(&qb, (size_t)nq * d * 2));
+        ANN_CUDA(bufs.alloc(&qn, (size_t)nq * 4));
         to_bf16_kernel<<<(unsigned)((nq * d + 255) / 256), 256, 0, s>>>(queries, nq * d, qb);
         norms_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(queries, nq, d, qn);
     }
@@ -512,14 +513,6 @@ int knn_u8_tensor(const uint8_t *refs, int64_t N, const uint8_t *queries, int64_
         cudaError_t e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) r = cuda_fail(e, "knn_tc_kernel");
-    }
-    cudaFreeAsync(hl, s);
-    cudaFreeAsync(rb, s);
-    cudaFreeAsync(rn, s);
-    cudaFreeAsync(derr, s);
-    if (!shared) {
-        cudaFreeAsync(qb, s);
-        cudaFreeAsync(qn, s);
     }
     if (r == ANN_OK && herr) r = fail(ANN_ERR_TIMEOUT, "knn_tc_kernel: a pipeline wait timed out");
     return r;

@@ -547,11 +547,11 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
         int capT = T_all;
         if (T) {
             int32_t *dmax = nullptr, hmax = 0;
-            ANN_CUDA(cudaMallocAsync((void **)&dmax, sizeof(int32_t), s));
+            AsyncBufs bufs(s);  // released at the end of this block
+            ANN_CUDA(bufs.alloc(&dmax, sizeof(int32_t)));
             ANN_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
             max_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, s>>>(T, nq, dmax);
             ANN_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            ANN_CUDA(cudaFreeAsync(dmax, s));
             ANN_CUDA(cudaStreamSynchronize(s));
             capT = hmax;
         }
@@ -607,11 +607,23 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
                 }
             }
         }
+        auto drop = [&p]() {
+            cudaFree(p.scratch);
+            if (p.wscratch) cudaFree(p.wscratch);
+        };
         cudaStream_t cap;
-        ANN_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t ce = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            drop();
+            return cuda_fail(ce, "cudaStreamCreateWithFlags");
+        }
         cudaGraph_t graph;
-        ANN_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce;
+        ce = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (ce != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            drop();
+            return cuda_fail(ce, "cudaStreamBeginCapture");
+        }
         int rr;
         {
             ForkSet fs;
@@ -621,15 +633,13 @@ extern "C" int ann_search_batch(const ann_index *index, const void *queries, int
         cudaStreamDestroy(cap);
         if (rr != ANN_OK || ce != cudaSuccess) {
             if (ce == cudaSuccess) cudaGraphDestroy(graph);
-            cudaFree(p.scratch);
-            if (p.wscratch) cudaFree(p.wscratch);
+            drop();
             return rr != ANN_OK ? rr : cuda_fail(ce, "cudaStreamEndCapture");
         }
         ce = cudaGraphInstantiate(&p.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ce != cudaSuccess) {
-            cudaFree(p.scratch);
-            if (p.wscratch) cudaFree(p.wscratch);
+            drop();
             return cuda_fail(ce, "cudaGraphInstantiate");
         }
         it = pc->plans.emplace(key, p).first;
