@@ -452,12 +452,39 @@ def main():
         extra = measure(args, rank, ws, log, torch, ann, datagen, W2, headline=False)
         extra = {k: extra[k] for k in ("config", "value", "ms_per_step", "plain", "persistent", "uneven", "roofline",
                                        "search_stats_mean_per_query", "e2e")}
+        extra["paper_dictionaries_4x50"] = paper_dictionaries(args, torch, ann, datagen, W2, log)
     if rank == 0:
         line = head["line"]
         if extra is not None:
             line["sift1m"] = extra
         print(json.dumps(line), flush=True)
     barrier(ws)
+
+
+def paper_dictionaries(args, torch, ann, datagen, W, log):
+    """The paper's own dictionary size for SIFT (Sec. 5.2: P = 4 parts of
+    n = 50 centers, k-means with 10 iterations) on the same 1M rows, exact
+    kNN graph and queries as the sift1m entry: T90 (bracketed and bisected
+    as for the headline), plain and persistent queries/s at T90 with k = 10,
+    and the index's bridge counts (Table 1's alpha)."""
+    C = ann.ann_train_centers(W["X"], 4, 50, 10, datagen.kmeans_init_rows(2, len(W["X"]), 50))
+    ix = ann.Index.create(W["X"], W["G"], C, t=100, b=5)
+    try:
+        T90, rec, table = sweep_t90(args, torch, ann, dict(W, index=ix), log)
+        log(f"sift1m, P = 4 x n = 50: T90={T90} recall@10={rec:.4f}")
+        stream = torch.cuda.Stream()
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = {}
+        for name, mode in (("plain", 0), ("persistent", 1)):
+            t = time_steps(torch, lambda: ann.ann_search_batch(ix, W["Q"], K, T90, kmax=K, mode=mode, stream=stream),
+                           args.steps, args.warmup, flush, stream)
+            out[name] = {"qps": W["nq"] * len(t) / (sum(t) / 1e3), "ms_per_step": statistics.mean(t)}
+        inf = ix.info()
+        return {"config": {"workload": "sift1m rows, kNN graph and queries; P = 4 x n = 50 dictionaries, b<=5, t=100",
+                           "T": T90, "k": K, "recall@10": rec, "recall_vs_T": table},
+                "M": inf["M"], "alpha": inf["alpha"], **out}
+    finally:
+        ix.free()
 
 
 WORKLOAD_NAMES = {
