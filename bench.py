@@ -437,10 +437,10 @@ def main():
     if args.build_only:
         torch.cuda.synchronize()
         return
-    if WORKLOAD in (3, 4):
-        return run_other(args, rank, ws, log, torch, ann, datagen, W)
     if args.ablation:
         return run_ablation(args, rank, ws, log, torch, ann, datagen, W)
+    if WORKLOAD in (3, 4):
+        return run_other(args, rank, ws, log, torch, ann, datagen, W)
     head = measure(args, rank, ws, log, torch, ann, datagen, W, headline=True)
     extra = None
     if WORKLOAD == 5 and not args.no_extra:
@@ -759,14 +759,17 @@ def run_other(args, rank, ws, log, torch, ann, datagen, W):
 
 
 def run_ablation(args, rank, ws, log, torch, ann, datagen, W):
-    """The paper's ablations on the SIFT-shaped 1M workload, same data, same
-    exact kNN graph, same queries: recall@10 and persistent queries/s versus
-    T for (a) the method (P = 4 x n = 256), (b) best-first graph search
-    without bridges, seeded at one fixed reference (a bridge graph of one
-    bridge holding reference 0), (c) P = 2 x n = 256 and (d) P = 4 x n = 50
-    dictionaries (k-means, 10 iterations, the same initial-row recipe)."""
+    """The paper's ablations on one workload (same data, same exact kNN graph,
+    same queries): recall@10 and persistent queries/s versus T for (a) the
+    method with the workload's configured dictionaries, (b) best-first graph
+    search without bridges, seeded at one fixed reference (a bridge graph of
+    one bridge holding reference 0), and the method with other dictionaries
+    (k-means, 10 iterations, the same initial-row recipe): P = 2 x n = 256
+    and P = 4 x n = 50 on sift1m, P = 4 x n = 50 (the paper's size for SIFT
+    and GIST, Sec. 5.2) elsewhere."""
     grid = [64, 128, 256, 512, 1024, 2048]
     X, Q, G = W["X"], W["Q"], W["G"]
+    spec = W["spec"]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -782,13 +785,16 @@ def run_ablation(args, rank, ws, log, torch, ann, datagen, W):
             log(f"{name}: T={T} recall@10={rec:.4f} {pts[-1]['qps']:.0f} q/s")
         return pts
 
-    out = {"method P=4 x n=256": curve(W["index"], "method 4x256")}
+    inf0 = W["index"].info()
+    P0, n0 = inf0["P"], inf0["n"]
+    out = {f"method P={P0} x n={n0} (M={inf0['M']}, alpha={inf0['alpha']:.3g})": curve(W["index"], f"{P0}x{n0}")}
     seed = {"bridges": np.array([0], np.uint64), "offsets": np.array([0, 1], np.int64),
             "refs": np.array([0], np.int32)}
     ix_seed = ann.Index.create(X, G, W["C"], t=100, b=5, bridges=seed)
     out["graph search, one seed (no bridges)"] = curve(ix_seed, "one seed")
     ix_seed.free()
-    for P, n in ((2, 256), (4, 50)):
+    others = ((2, 256), (4, 50)) if WORKLOAD == 2 else ((4, 50),)
+    for P, n in others:
         C = ann.ann_train_centers(X, P, n, 10, datagen.kmeans_init_rows(WORKLOAD, len(X), n))
         ix = ann.Index.create(X, G, C, t=100, b=5)
         inf = ix.info()
@@ -796,7 +802,8 @@ def run_ablation(args, rank, ws, log, torch, ann, datagen, W):
         ix.free()
     if rank == 0:
         print(json.dumps({"metric": "recall@10 and queries/s versus T (ablation)", "unit": "queries/s",
-                          "workload": f"sift1m: N={W['N']} x 128 uint8, {W['nq']} queries, kNN graph R=20, k=10",
+                          "workload": f"{spec['name']}: N={W['N']} x {X.shape[1]} {str(X.dtype).replace('torch.', '')}, "
+                                      f"{W['nq']} queries, kNN graph R={G.shape[1]}, k={K}",
                           "mode": "persistent", "curves": out}), flush=True)
     barrier(ws)
 
