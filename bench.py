@@ -66,8 +66,8 @@ def parse():
     ap.add_argument("--build-only", action="store_true", help="build the index and exit (profiling the build)")
     ap.add_argument("--Tlist", default=None, help="workload 4: comma-separated budgets instead of 256,1024,4096")
     ap.add_argument("--ablation", action="store_true",
-                    help="sift1m: recall@10 and queries/s versus T for the method, for graph search without "
-                         "bridges (one seed), and for other part dictionaries (P x n)")
+                    help="the workload's recall@10 and queries/s versus T for the method, for graph search "
+                         "without bridges (one seed), and for other part dictionaries (P x n)")
     ap.add_argument("--knn-approx", action="store_true",
                     help="workload 2 or 5: approximate kNN graph versus the exact one (build time, graph "
                          "recall; on workload 2 also the search each graph gives)")
